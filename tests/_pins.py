@@ -1,0 +1,257 @@
+"""Pins of the CPU oracle to facts outside itself.
+
+Each pin takes an ``oracle.OracleLib`` and raises AssertionError if the oracle
+disagrees with something the paper or mathematics fixes:
+
+* the sample code table of Appendix A (golden file);
+* a library routine on a different formulation: numpy's complex matrix
+  product X @ X^H (V_ij = sum_t x_i conj(x_j) is exactly that product);
+* invariants: Hermitian symmetry, real non-negative autos equal to sum |x|^2,
+  rank one at T = 1, additivity over time, permutation equivariance;
+* closed forms: constant inputs give T c_i conj(c_j); an injected tone of known
+  per-input phase gives arg V_ij = phi_i - phi_j within the rounding bound;
+* the invalid-sample reading (code 8) and the output sizes printed in
+  Section 3.4.3.
+
+The same pins run against deliberately broken copies of the oracle source
+(tests/test_oracle_pins.py::test_pins_catch_planted_mistakes) to show that each
+plausible mistake is caught by at least one of them.
+"""
+from __future__ import annotations
+
+import math
+import os
+
+import numpy as np
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+
+
+def read_table(name: str) -> list[list[str]]:
+    rows = []
+    with open(os.path.join(GOLDEN, name)) as f:
+        for line in f:
+            line = line.split("#", 1)[0].strip()
+            if line:
+                rows.append(line.split())
+    return rows
+
+
+def code_values() -> np.ndarray:
+    vals = np.zeros(16, np.int64)
+    for code, value in read_table("nibble_codes.txt"):
+        vals[int(code)] = int(value)
+    return vals
+
+
+def numpy_decode(volt: np.ndarray, zero_invalid: bool = False) -> np.ndarray:
+    """Complex128 samples from the golden code table (independent of the oracle)."""
+    vals = code_values()
+    hi = (volt >> 4) & 0xF
+    lo = volt & 0xF
+    x = vals[hi].astype(np.float64) + 1j * vals[lo].astype(np.float64)
+    if zero_invalid:
+        x[(hi == 8) | (lo == 8)] = 0
+    return x
+
+
+def tri_index(i: int, j: int) -> int:
+    return i * (i + 1) // 2 + j
+
+
+def tri_to_full(tri: np.ndarray, n: int) -> np.ndarray:
+    """[F][P][2] packed lower triangle -> complex [F][N][N] using V_ji = conj(V_ij)."""
+    F = tri.shape[0]
+    out = np.zeros((F, n, n), np.complex128)
+    ii, jj = np.tril_indices(n)
+    p = ii * (ii + 1) // 2 + jj
+    v = tri[:, p, 0].astype(np.float64) + 1j * tri[:, p, 1].astype(np.float64)
+    out[:, ii, jj] = v
+    out[:, jj, ii] = np.conj(v)
+    return out
+
+
+def _rng(seed):
+    return np.random.default_rng(seed)
+
+
+# ------------------------------------------------------------------ pins ---
+def pin_decode_table(o):
+    b = np.arange(256, dtype=np.uint8).reshape(1, 1, 256)
+    re, im = o.decode(b)
+    vals = code_values()
+    assert np.array_equal(re.ravel(), vals[np.arange(256) >> 4]), "real part must be the high nibble"
+    assert np.array_equal(im.ravel(), vals[np.arange(256) & 15]), "imag part must be the low nibble"
+
+
+def pin_library_matmul(o):
+    rng = _rng(11)
+    for (T, F, N) in [(37, 3, 7), (1, 2, 5), (64, 2, 16), (5, 1, 1)]:
+        volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+        tri = o.xmac(volt)
+        x = numpy_decode(volt)                               # [T][F][N]
+        for f in range(F):
+            X = x[:, f, :].T                                 # [N][T]
+            V = X @ X.conj().T                               # library complex GEMM
+            got = tri_to_full(tri[f:f + 1], N)[0]
+            assert np.array_equal(got, V), f"oracle != X X^H for shape {(T, F, N)}"
+
+
+def pin_hermitian(o):
+    rng = _rng(12)
+    volt = rng.integers(0, 256, (23, 2, 9), dtype=np.uint8)
+    full = o.xmac_full(volt)
+    v = full[..., 0] + 1j * full[..., 1]
+    assert np.array_equal(v, np.conj(np.swapaxes(v, 1, 2))), "V_ij != conj(V_ji)"
+    tri = o.xmac(volt)
+    n = volt.shape[2]
+    for i in range(n):
+        for j in range(i + 1):
+            assert tuple(tri[:, tri_index(i, j)].tolist()[0]) == tuple(full[0, i, j]), \
+                "packed triangle entry differs from the full matrix"
+
+
+def pin_autos(o):
+    rng = _rng(13)
+    volt = rng.integers(0, 256, (41, 3, 6), dtype=np.uint8)
+    tri = o.xmac(volt)
+    x = numpy_decode(volt)
+    for i in range(volt.shape[2]):
+        p = tri_index(i, i)
+        assert np.all(tri[:, p, 1] == 0), "autocorrelation must be real"
+        want = np.sum(np.abs(x[:, :, i]) ** 2, axis=0)
+        assert np.array_equal(tri[:, p, 0].astype(np.float64), want), "auto != sum |x|^2"
+
+
+def pin_constant_closed_form(o):
+    vals = code_values()
+    rng = _rng(14)
+    N, T = 6, 97
+    codes = rng.integers(0, 256, N, dtype=np.uint8)
+    volt = np.broadcast_to(codes, (T, 1, N)).copy()
+    tri = o.xmac(volt)
+    c = [complex(int(vals[b >> 4]), int(vals[b & 15])) for b in codes]
+    for i in range(N):
+        for j in range(i + 1):
+            want = T * c[i] * c[j].conjugate()
+            got = tri[0, tri_index(i, j)]
+            assert (int(got[0]), int(got[1])) == (int(want.real), int(want.imag)), \
+                "constant input does not give T c_i conj(c_j)"
+
+
+def pin_rank_one(o):
+    rng = _rng(15)
+    volt = rng.integers(0, 256, (1, 4, 8), dtype=np.uint8)
+    V = tri_to_full(o.xmac(volt), 8)
+    for f in range(4):
+        d = np.real(np.diag(V[f]))
+        mag2 = V[f].real ** 2 + V[f].imag ** 2          # exact for these integers
+        assert np.array_equal(mag2, np.outer(d, d)), "T=1 matrix is not rank one"
+
+
+def pin_additivity(o):
+    rng = _rng(16)
+    a = rng.integers(0, 256, (30, 2, 7), dtype=np.uint8)
+    b = rng.integers(0, 256, (19, 2, 7), dtype=np.uint8)
+    whole = o.xmac(np.concatenate([a, b], axis=0))
+    assert np.array_equal(whole, o.xmac(a) + o.xmac(b)), "integration is not additive in time"
+    acc = o.xmac(a)
+    o.xmac(b, vis=acc)
+    assert np.array_equal(whole, acc), "accumulate-into differs from one call"
+
+
+def pin_permutation(o):
+    rng = _rng(17)
+    N = 9
+    volt = rng.integers(0, 256, (25, 2, N), dtype=np.uint8)
+    perm = rng.permutation(N)
+    V = tri_to_full(o.xmac(volt), N)
+    W = tri_to_full(o.xmac(volt[:, :, perm]), N)
+    assert np.array_equal(W, V[:, perm][:, :, perm]), "not permutation equivariant"
+
+
+def pin_tone_phase(o):
+    """x_k(t) = round(A exp(i(w t + phi_k))): arg V_ij within 2 asin(sqrt2/(2A)) of phi_i - phi_j."""
+    A, T, N = 7.0, 400, 8
+    w = 2 * math.pi * 0.0371
+    phi = 2 * math.pi * np.arange(N) / N + 0.3
+    t = np.arange(T)[:, None]
+    z = A * np.exp(1j * (w * t + phi[None, :]))
+    r = np.clip(np.round(z.real), -7, 7).astype(np.int64)
+    m = np.clip(np.round(z.imag), -7, 7).astype(np.int64)
+    volt = (((r & 0xF) << 4) | (m & 0xF)).astype(np.uint8)[:, None, :]
+    V = tri_to_full(o.xmac(volt), N)[0]
+    delta = math.sqrt(2) / 2
+    ang_bound = 2 * math.asin(delta / A)
+    for i in range(N):
+        for j in range(N):
+            d = (np.angle(V[i, j]) - (phi[i] - phi[j]) + math.pi) % (2 * math.pi) - math.pi
+            assert abs(d) <= ang_bound + 1e-12, f"phase of V_{i}{j} off by {d}"
+            mag = abs(V[i, j])
+            assert T * (A - delta) ** 2 * math.cos(ang_bound) - 1e-9 <= mag <= T * (A + delta) ** 2, \
+                f"|V_{i}{j}| = {mag} outside the rounding bounds"
+
+
+def pin_invalid_reading(o):
+    rng = _rng(18)
+    volt = rng.integers(0, 256, (33, 2, 5), dtype=np.uint8)
+    volt[3, 0, 1] = 0x80
+    volt[4, 1, 2] = 0x08
+    volt[5, 0, 0] = 0x88
+    volt[6, 1, 4] = 0x83
+    bad = (((volt >> 4) & 0xF) == 8) | ((volt & 0xF) == 8)
+    clean = np.where(bad, np.uint8(0), volt)
+    assert np.array_equal(o.xmac(volt, zero_invalid=True), o.xmac(clean)), \
+        "zero_invalid must zero every sample with a nibble equal to 8"
+    assert not np.array_equal(o.xmac(volt), o.xmac(clean)), "default must decode code 8 as -8"
+    x = numpy_decode(volt)
+    X = x[:, 0, :].T
+    assert np.array_equal(tri_to_full(o.xmac(volt)[0:1], 5)[0], X @ X.conj().T)
+
+
+def pin_paper_sizes(o):
+    d = {k: float(v) for k, v in read_table("paper_sizes.txt")}
+    n = int(d["inputs"])
+    S, Pp = int(d["stations"]), int(d["pols"])
+    assert n == S * Pp
+    volt = np.zeros((1, 1, n), np.uint8)
+    P = o.xmac(volt).shape[1]
+    assert P == n * (n + 1) // 2
+    # station-pair products (s1 >= s2, p1, p2) of Appendix C map onto the flat
+    # input triangle (n = 2 s + p); the paper's count includes both cross-pol
+    # products of each station with itself, one of which is the conjugate of
+    # the other: 33024 = N(N+1)/2 + stations.
+    hits = np.zeros(P, np.int64)
+    for s1 in range(S):
+        for s2 in range(s1 + 1):
+            for p1 in range(Pp):
+                for p2 in range(Pp):
+                    a, b = Pp * s1 + p1, Pp * s2 + p2
+                    hits[tri_index(max(a, b), min(a, b))] += 1
+    assert hits.sum() == int(d["visibilities_per_channel"])
+    assert np.all(hits >= 1) and np.count_nonzero(hits == 2) == S
+    total = d["visibilities_per_channel"] * d["channels"] * d["bytes_per_visibility"]
+    assert abs(total - d["approx_bytes_per_time_unit"]) / d["approx_bytes_per_time_unit"] < 0.05
+
+
+def pin_brute_force(o):
+    rng = _rng(19)
+    vals = code_values()
+    volt = rng.integers(0, 256, (6, 2, 4), dtype=np.uint8)
+    tri = o.xmac(volt)
+    for f in range(2):
+        for i in range(4):
+            for j in range(i + 1):
+                s = 0j
+                for t in range(6):
+                    bi, bj = int(volt[t, f, i]), int(volt[t, f, j])
+                    xi = complex(int(vals[bi >> 4]), int(vals[bi & 15]))
+                    xj = complex(int(vals[bj >> 4]), int(vals[bj & 15]))
+                    s += xi * xj.conjugate()
+                got = tri[f, tri_index(i, j)]
+                assert (int(got[0]), int(got[1])) == (int(s.real), int(s.imag))
+
+
+ALL_PINS = [pin_decode_table, pin_library_matmul, pin_hermitian, pin_autos,
+            pin_constant_closed_form, pin_rank_one, pin_additivity, pin_permutation,
+            pin_tone_phase, pin_invalid_reading, pin_paper_sizes, pin_brute_force]
