@@ -1,0 +1,382 @@
+#!/usr/bin/env python3
+"""Benchmark of the X-engine hot path: complex MAC/s and x real time.
+
+Workload (default "full_band"): 256 inputs x 3072 fine channels, 16
+consecutive integrations of 5000 samples (0.5 s at 10 kHz), 4+4-bit voltages
+from the seeded gauss3 recipe, generated in device memory before timing.  One
+step = 16 x (corr_accumulate of one integration + corr_dump of its packed
+triangle): the whole hot path over 8 s of data (62.9 GB of voltages, larger
+than L2, so no flush is needed between steps).
+
+Prints one JSON line (rank 0).  `value` is device-resident throughput, `e2e`
+the same metric through the host-buffer C-ABI calls (host->device copies of
+every step's voltages and device->host copies of every dump inside the timed
+region).  `--impl reference` times the CPU oracle on a bounded sample instead.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "Correlator CMAC/s and ×real-time, 256 inputs×3072 ch; TC vs CUDA-core, bit-exact"
+UNIT = "CMAC/s"
+SAMPLE_RATE_HZ = 1.0e4            # 10 kHz fine channels: one sample per channel per 100 us
+
+WORKLOADS = {
+    # name: (n_inputs, n_chan, samples per integration, integrations, recipe seed)
+    "full_band": (256, 3072, 5000, 16, 1503),
+    "coarse_channel": (256, 128, 5000, 1, 1502),
+}
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__)
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
+    ap.add_argument("--path", default="auto", choices=["auto", "cudacore", "mma_i8", "tc_fp8"])
+    ap.add_argument("--workload", default="full_band", choices=sorted(WORKLOADS))
+    ap.add_argument("--e2e-steps", type=int, default=2)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target CPU time of the oracle baseline sample")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+# ---------------------------------------------------------------- clocks ---
+class ClockSampler:
+    """nvidia-smi clock / throttle sampling while the timed region runs."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device_index: int):
+        self.idx = device_index
+        self.proc = None
+        self.lines: list[str] = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self._t = threading.Thread(target=self._read, daemon=True)
+            self._t.start()
+        except (FileNotFoundError, OSError):
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self) -> dict | None:
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self._t.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in self.lines:
+            parts = [p.strip() for p in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, val in zip(names, parts[5:9]):
+                if val.lower() == "active":
+                    reasons.add(name)
+        if not sm:
+            return None
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(smax),
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ------------------------------------------------------------ distributed ---
+def dist_setup(args):
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        import torch.distributed as dist
+        backend = "nccl" if args.impl == "ours" else "gloo"
+        import torch
+        if args.impl == "ours":
+            torch.cuda.set_device(local)
+        dist.init_process_group(backend=backend)
+    return world, rank, local
+
+
+def barrier(world):
+    if world > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def max_over_ranks(x: float, world: int) -> float:
+    if world == 1:
+        return x
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+# ----------------------------------------------------------- CPU baseline ---
+def oracle_sample(volt_host_slab, seconds_budget: float):
+    """Time the oracle on channels of one integration: returns (CMAC/s, cores, sample str)."""
+    import numpy as np
+    import oracle
+    T, F, N = volt_host_slab.shape
+    P = N * (N + 1) // 2
+    probe = np.ascontiguousarray(volt_host_slab[:, :2, :])
+    t0 = time.perf_counter()
+    oracle.xmac(probe)
+    per_chan = (time.perf_counter() - t0) / 2
+    k = int(max(2, min(F, seconds_budget / max(per_chan, 1e-6))))
+    sample = np.ascontiguousarray(volt_host_slab[:, :k, :])
+    t0 = time.perf_counter()
+    oracle.xmac(sample)
+    dt = time.perf_counter() - t0
+    cmac = P * k * T
+    desc = f"{k} channels x {T} samples x {N} inputs of integration 0 ({cmac:.3e} CMAC, {dt:.1f} s)"
+    return cmac / dt, oracle.threads(), desc
+
+
+def host_sample_slab(n_inputs, n_chan, n_time, seed, channels):
+    from synth import voltgen as vg
+    p = vg.gauss3_params(seed, n_inputs, n_chan)
+    return vg.gauss3(p, 0, n_time, 0, channels)
+
+
+def run_reference(args, world, rank):
+    if rank != 0:
+        return
+    n_inputs, n_chan, t_int, n_int, seed = WORKLOADS[args.workload]
+    P = n_inputs * (n_inputs + 1) // 2
+    import oracle
+    oracle.build()
+    slab = host_sample_slab(n_inputs, n_chan, t_int, seed, channels=min(n_chan, 64))
+    budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
+    for _ in range(args.warmup):
+        oracle_sample(slab[:, :2], 0.5)
+    rates, descs, cores = [], [], 1
+    for _ in range(args.steps):
+        r, cores, d = oracle_sample(slab, min(budget, args.cpu_seconds))
+        rates.append(r)
+        descs.append(d)
+    value = statistics.median(rates)
+    step_cmac = P * n_chan * t_int * n_int
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": step_cmac / value * 1e3, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+        "x_real_time": value / (P * n_chan * SAMPLE_RATE_HZ),
+        "config": workload_config(args, "oracle (CPU, int64 triple loop)"),
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
+                         "sample": descs[-1]},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def workload_config(args, path):
+    n_inputs, n_chan, t_int, n_int, seed = WORKLOADS[args.workload]
+    return {"workload": f"{args.workload}: {n_inputs} inputs x {n_chan} ch x {n_int} integrations "
+                        f"x {t_int} samples (4+4-bit, gauss3 recipe, seed {seed})",
+            "n_inputs": n_inputs, "n_chan": n_chan, "samples_per_integration": t_int,
+            "integrations_per_step": n_int, "path": path,
+            "l2": "no flush: each step reads %.1f GB of voltages (> 129 MB L2)"
+                  % (n_inputs * n_chan * t_int * n_int / 1e9),
+            "parallelism": "replicas (channels shard with no exchange)"}
+
+
+# ------------------------------------------------------------------ ours ---
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+
+
+def load_peaks():
+    try:
+        with open(PEAKS_FILE) as f:
+            return json.load(f), "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0,
+                "sm_max_mhz": 2070.0}, "fallback"
+
+
+def roofline_for(path, ops_per_launch, avg_ms, peaks, src, sm_count):
+    achieved = ops_per_launch / (avg_ms * 1e-3) / 1e12          # Tops/s
+    if path == "tc_fp8":
+        peak = peaks["bf16_tflops_sustained"] * 2.0              # fp8 = 2 x bf16 (nominal ratio)
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak,
+                "peak_note": f"fp8 dense = 2 x bf16 sustained ({src}); ops = 8 per useful CMAC"}
+    if path == "mma_i8":
+        peak = peaks["bf16_tflops_sustained"] * 2.0
+        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TOPS",
+                "frac": achieved / peak,
+                "peak_note": f"int8 taken at the nominal 2 x bf16 sustained ({src}); "
+                             "ops = 8 per useful CMAC"}
+    # dp4a: one 4-way int8 dot product per lane per clock (upper bound)
+    peak = sm_count * 128 * 4 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+    return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOPS",
+            "frac": achieved / peak,
+            "peak_note": f"{sm_count} SMs x 128 lanes x 1 dp4a (8 ops) per clock at "
+                         f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"}
+
+
+def run_ours(args, world, rank, local):
+    import torch
+    from paper_1501_05992_gb300 import corr
+    from synth import voltgen as vg
+    from synth.gpu import DeviceGenerator
+
+    dev = torch.device("cuda", local)
+    torch.cuda.set_device(dev)
+    n_inputs, n_chan, t_int, n_int, seed = WORKLOADS[args.workload]
+    P = n_inputs * (n_inputs + 1) // 2
+    T_total = t_int * n_int
+    # every rank correlates its own array (weak scaling, no exchange)
+    params = vg.gauss3_params(seed, n_inputs, n_chan, array=rank)
+    gen = DeviceGenerator(params, dev)
+    volt = torch.empty((T_total, n_chan, n_inputs), dtype=torch.uint8, device=dev)
+    for k in range(n_int):
+        gen.fill(volt[k * t_int:(k + 1) * t_int], t0=k * t_int)
+    outs = [torch.empty((n_chan, P, 2), dtype=torch.int32, device=dev) for _ in range(2)]
+    c = corr.Correlator(n_inputs, n_chan, t_int, path=args.path, device=dev)
+    path = c.path
+    stream = torch.cuda.current_stream(dev)
+
+    def step():
+        for k in range(n_int):
+            c.accumulate(volt[k * t_int:(k + 1) * t_int])
+            c.dump(outs[k & 1])
+
+    for _ in range(args.warmup):
+        step()
+    c.sync()
+    torch.cuda.synchronize(dev)
+    c.profile_read(reset=True)
+    c.profile_enable(True)
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    barrier(world)
+    torch.cuda.synchronize(dev)
+    if clocks:
+        clocks.start()
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(world)
+    clk = clocks.stop() if clocks else None
+    c.profile_enable(False)
+    prof = c.profile_read(reset=True)
+    c.sync()
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
+    step_cmac = P * n_chan * T_total
+    value = step_cmac * args.steps * world / (elapsed_ms * 1e-3)
+    launches = sum(v["launches"] for v in prof.values())
+
+    xe = prof["xengine"]
+    peaks, src = load_peaks()
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    ops_total = 8.0 * step_cmac * args.steps
+    roof = roofline_for(path, ops_total / max(1, xe["timed"]), xe["ms"] / max(1, xe["timed"]),
+                        peaks, src, sm_count)
+    roof["traffic"] = None
+    roof["kernel"] = {"cudacore": "xeng_dp4a_kernel", "mma_i8": "xeng_mma8_kernel",
+                      "tc_fp8": "xeng_tc_kernel"}[path]
+    roof["launches"] = xe["timed"]
+    roof["avg_launch_ms"] = xe["ms"] / max(1, xe["timed"])
+
+    # ---- end to end through the host-buffer C-ABI calls -------------------
+    e2e = None
+    if args.e2e_steps > 0:
+        h_volt = volt[:t_int].cpu().pin_memory()          # one integration, reused
+        h_outs = [torch.empty((n_chan, P, 2), dtype=torch.int32).pin_memory() for _ in range(2)]
+
+        def step_host():
+            for k in range(n_int):
+                c.accumulate_host(h_volt)
+                c.dump_host(h_outs[k & 1])
+
+        step_host()
+        c.sync()
+        barrier(world)
+        torch.cuda.synchronize(dev)
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        t0 = time.perf_counter()
+        e0.record(stream)
+        for _ in range(args.e2e_steps):
+            step_host()
+        e1.record(stream)
+        torch.cuda.synchronize(dev)
+        wall = time.perf_counter() - t0
+        e_ms = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3), world)
+        e2e = {"value": step_cmac * args.e2e_steps * world / (e_ms * 1e-3), "unit": UNIT,
+               "h2d_bytes_per_step": n_int * t_int * n_chan * n_inputs,
+               "d2h_bytes_per_step": n_int * n_chan * P * 8,
+               "note": "host voltages: one pinned integration re-sent 16 times per step"}
+        del h_volt, h_outs
+
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        slab = volt[:t_int, :min(n_chan, 256)].cpu().numpy()
+        rate, cores, desc = oracle_sample(slab, args.cpu_seconds)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"cudacore": "int8", "mma_i8": "int8", "tc_fp8": "e4m3"}[path],
+            "data": "synthetic", "x_real_time": value / (P * n_chan * SAMPLE_RATE_HZ * world),
+            "config": workload_config(args, path),
+            "gpu_launches": launches, "clocks": clk, "roofline": roof,
+            "cpu_baseline": cpu, "e2e": e2e, "kernel_ms": {k: v["ms"] for k, v in prof.items()},
+        }
+        print(json.dumps(line), flush=True)
+    c.close()
+
+
+def main():
+    args = parse_args()
+    world, rank, local = dist_setup(args)
+    try:
+        if args.impl == "reference":
+            run_reference(args, world, rank)
+        else:
+            run_ours(args, world, rank, local)
+    finally:
+        if world > 1:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

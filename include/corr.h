@@ -1,0 +1,219 @@
+/*
+ * corr.h -- C ABI of the GB300 X-engine library (libcorr.so).
+ *
+ * The library implements the cross-multiply-and-accumulate stage of an FX
+ * correlator for 4+4-bit complex channelised voltages: for every fine
+ * frequency channel f and every input pair 0 <= j <= i < N it accumulates
+ *
+ *     V_ij(f) = sum_t x_i(t,f) * conj(x_j(t,f))                       (1)
+ *
+ * over an integration and emits the packed lower triangle including the
+ * autocorrelations.  Eq. 3 (Section 2) is the per-channel product of two
+ * spectra; Section 3.4.2 integrates the products over a time I on the GPU;
+ * Appendix C ("GPU Output") fixes the packed-triangle output.  The arithmetic
+ * here is exact integer arithmetic, so every result equals the int64
+ * reference sum bit for bit.
+ *
+ * Conventions shared by every call below
+ * -------------------------------------
+ * Voltage input (Appendix A "Data Format", Appendix C "GPU Input"):
+ *   uint8 volt[n_time][n_chan][n_inputs], one byte per complex sample, real
+ *   part = high nibble (bits 7..4), imaginary part = low nibble (bits 3..0),
+ *   each 4-bit two's complement (-8..7).  The input index is
+ *   n = 2*station + polarisation; the library is agnostic to input order
+ *   (Appendix C: the GPU correlates in whatever order the inputs arrive).
+ *   Nibble code 8 is the paper's "invalid" marker: by default it decodes as
+ *   -8; with CORR_ZERO_INVALID a sample with either nibble equal to 8 is
+ *   treated as 0 + 0i.
+ *
+ * Visibility output:
+ *   int32 vis[n_chan][P][2], P = N(N+1)/2, element (i, j), j <= i, at index
+ *   i(i+1)/2 + j, holding (Re, Im) of (1) with x_i unconjugated.
+ *
+ * Memory ownership: the caller owns every buffer it passes.  Device buffers
+ * are plain device pointers (cudaMalloc or a framework allocator); the
+ * library never frees or retains them beyond the call, except the workspace
+ * bound with corr_bind_workspace, which it uses until the context is
+ * destroyed or another workspace is bound.  The library itself allocates only
+ * host memory for the context object; every device byte it touches is the
+ * caller's.
+ *
+ * Streams: `stream` is a cudaStream_t passed as void* (NULL = legacy default
+ * stream).  Calls enqueue work and return without synchronising the host,
+ * except corr_sync, corr_get_state and corr_set_state which synchronise the
+ * given stream.  Argument and state errors are detected on the host and
+ * returned synchronously before anything is enqueued.
+ *
+ * Errors: every call returns a corr_status (0 = success, negative = error)
+ * and records it for corr_last_error() in the calling thread.  No call
+ * aborts, exits or prints.
+ */
+#ifndef CORR_H
+#define CORR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum corr_status {
+    CORR_OK = 0,
+    CORR_E_ARG = -1,          /* invalid argument (NULL, size, alignment)        */
+    CORR_E_STATE = -2,        /* call not valid in the context's current state   */
+    CORR_E_OVERFLOW = -3,     /* integration would exceed n_time_per_int         */
+    CORR_E_NOMEM = -4,        /* host allocation failed / workspace too small    */
+    CORR_E_BUDGET = -5,       /* request exceeds a caller-set memory budget      */
+    CORR_E_CUDA = -6,         /* a CUDA runtime call failed                      */
+    CORR_E_TIMEOUT = -7,      /* a bounded device-side wait gave up              */
+    CORR_E_UNSUPPORTED = -8   /* shape or path not supported on this device      */
+} corr_status;
+
+/* X-engine implementations (all bit-exact). */
+typedef enum corr_path {
+    CORR_PATH_AUTO = 0,       /* fastest supported path for the shape            */
+    CORR_PATH_CUDACORE = 1,   /* register-tiled dp4a on CUDA cores (baseline)    */
+    CORR_PATH_MMA_I8 = 2,     /* int8 warp-level mma.sync, int32 accumulation    */
+    CORR_PATH_TC_FP8 = 3      /* tcgen05 E4M3 tensor cores, FP32 in TMEM         */
+} corr_path;
+
+/* Context flags (corr_set_flags). */
+#define CORR_ZERO_INVALID 1u
+
+typedef struct corr_ctx corr_ctx;
+
+/* ---------------------------------------------------------------- context -- */
+
+/*
+ * Create a context for an array of n_inputs inputs and n_chan fine channels
+ * integrating at most n_time_per_int samples per dump.  Binds to the current
+ * CUDA device.  Returns NULL on error (corr_last_error() tells which):
+ * CORR_E_ARG if any size is < 1 or 128 * n_time_per_int >= 2^31 (the int32
+ * bound for |Re V_ij| when every component is -8), CORR_E_NOMEM if the host
+ * context cannot be allocated, CORR_E_CUDA if no device is usable.
+ */
+corr_ctx *corr_create(int n_inputs, int n_chan, int n_time_per_int);
+
+/* Release the context (host memory only; the workspace stays the caller's). */
+int corr_destroy(corr_ctx *ctx);
+
+/* Select the implementation.  CORR_E_UNSUPPORTED if the path cannot run this
+ * shape on this device (e.g. CORR_PATH_TC_FP8 needs n_inputs % 16 == 0 and a
+ * sm_103 device).  Valid only between integrations (corr_samples() == 0),
+ * else CORR_E_STATE.  The default is CORR_PATH_AUTO. */
+int corr_set_path(corr_ctx *ctx, int path);
+
+/* The path that accumulate calls will run (AUTO resolved). */
+int corr_get_path(const corr_ctx *ctx);
+
+/* Set CORR_* flags (only between integrations, else CORR_E_STATE). */
+int corr_set_flags(corr_ctx *ctx, unsigned flags);
+
+/* Bytes of device workspace the context needs for its current path (int32
+ * accumulators, unpacked operand staging, host-transfer staging, status
+ * word).  The caller allocates at least this many bytes, 256-byte aligned. */
+size_t corr_workspace_bytes(const corr_ctx *ctx);
+
+/* Give the context its workspace (device pointer, caller-owned).  Resets the
+ * integration (the accumulators are treated as zero).  CORR_E_ARG if d_ws is
+ * NULL, not 256-byte aligned, or bytes < corr_workspace_bytes(). */
+int corr_bind_workspace(corr_ctx *ctx, void *d_ws, size_t bytes);
+
+/* ------------------------------------------------------------ integration -- */
+
+/*
+ * Add n_time samples of every channel and input to the running integration:
+ * d_volt is a device pointer to uint8 [n_time][n_chan][n_inputs] (layout
+ * above).  n_time == 0 is a no-op.  CORR_E_OVERFLOW (nothing enqueued) if
+ * corr_samples() + n_time > n_time_per_int; CORR_E_STATE if no workspace is
+ * bound; CORR_E_ARG on NULL d_volt or negative n_time.  Asynchronous.
+ */
+int corr_accumulate(corr_ctx *ctx, const uint8_t *d_volt, int n_time, void *stream);
+
+/*
+ * Write the current integration's packed triangle to d_vis (device int32
+ * [n_chan][P][2]) and start a new integration.  Valid at any time, including
+ * on a partial or empty integration (an empty one dumps zeros).
+ */
+int corr_dump(corr_ctx *ctx, int32_t *d_vis, void *stream);
+
+/* Samples accumulated since the last dump (host-side count). */
+long long corr_samples(const corr_ctx *ctx);
+
+/*
+ * End-to-end variants over HOST buffers: h_volt is host memory
+ * [n_time][n_chan][n_inputs] (pinned memory gives full copy bandwidth); the
+ * library copies it through the workspace's device staging ring in chunks,
+ * overlapping each chunk's host-to-device copy with the previous chunk's
+ * correlation, all on `stream`.  corr_dump_host copies the triangle to host
+ * memory h_vis.  Both are asynchronous like their device counterparts: the
+ * host buffers must stay valid and unmodified until the stream reaches the
+ * end of the enqueued work.
+ */
+int corr_accumulate_host(corr_ctx *ctx, const uint8_t *h_volt, int n_time, void *stream);
+int corr_dump_host(corr_ctx *ctx, int32_t *h_vis, void *stream);
+
+/* Synchronise `stream`, then report a device-side error recorded by a kernel
+ * of this context (CORR_E_TIMEOUT if a bounded wait gave up) or CORR_OK. */
+int corr_sync(corr_ctx *ctx, void *stream);
+
+/* ------------------------------------------------------ checkpoint/resume -- */
+
+/* Size of the serialised integration state: a 32-byte header (magic, N, F,
+ * samples) followed by the int32 accumulators [n_chan][P][2]. */
+size_t corr_state_bytes(const corr_ctx *ctx);
+
+/* Copy the running integration to host memory h_buf (synchronises stream). */
+int corr_get_state(corr_ctx *ctx, void *h_buf, size_t bytes, void *stream);
+
+/* Restore an integration saved by corr_get_state from a context of the same
+ * shape (CORR_E_ARG on a size or header mismatch; synchronises stream). */
+int corr_set_state(corr_ctx *ctx, const void *h_buf, size_t bytes, void *stream);
+
+/* ------------------------------------------------------------- stand-alone -- */
+
+/*
+ * Unpack and corner-turn (the GPU form of the host-side reordering and 4-to-8
+ * bit promotion of Section 3.4.1 and Appendix C "GPU Input"): reads d_volt
+ * uint8 [n_time][n_chan][n_inputs] and writes d_out int8
+ * [n_chan][n_inputs][n_time][2] (real, imaginary), time contiguous per input.
+ * flags: CORR_ZERO_INVALID or 0.  d_out must hold 2*n_time*n_chan*n_inputs
+ * bytes.  Asynchronous.
+ */
+int corr_unpack(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs,
+                int8_t *d_out, unsigned flags, void *stream);
+
+/* --------------------------------------------------------------- profiling -- */
+
+/* Kernel kinds counted by the profiler. */
+enum { CORR_K_UNPACK = 0, CORR_K_XENGINE = 1, CORR_K_DUMP = 2, CORR_K_OTHER = 3, CORR_K_KINDS = 4 };
+
+typedef struct corr_profile {
+    long long launches[CORR_K_KINDS];  /* kernels launched by this context, by kind */
+    long long timed[CORR_K_KINDS];     /* of which bracketed by timing events       */
+    double ms[CORR_K_KINDS];           /* summed device time of the timed launches  */
+} corr_profile;
+
+/* Launch counting is always on.  With on != 0 every kernel launch of the
+ * context is also bracketed by a pair of CUDA events recorded on the launch
+ * stream (device-side timing, no host synchronisation at launch). */
+int corr_profile_enable(corr_ctx *ctx, int on);
+
+/* Fill *out with the counts and the summed event times since the last reset
+ * (waits for the recorded events to complete); reset != 0 clears them. */
+int corr_profile_read(corr_ctx *ctx, corr_profile *out, int reset);
+
+/* ------------------------------------------------------------------ errors -- */
+
+int corr_last_error(void);            /* last status returned in this thread */
+const char *corr_strerror(int status);  /* static string, never NULL         */
+
+/* Library version as 10000*major + 100*minor + patch. */
+int corr_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* CORR_H */

@@ -1,0 +1,285 @@
+"""Python binding of libcorr.so (include/corr.h): argument marshalling only.
+
+Every step of the X-engine runs in the library's CUDA kernels; this module
+turns torch tensors into device pointers, torch streams into cudaStream_t
+handles, and status codes into exceptions.  PyTorch supplies device memory
+(the workspace and output tensors) and streams, nothing else.  If the library
+is not built, or its calls fail, these functions raise: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+import torch
+
+from . import build as _build
+
+CORR_OK = 0
+CORR_E_ARG = -1
+CORR_E_STATE = -2
+CORR_E_OVERFLOW = -3
+CORR_E_NOMEM = -4
+CORR_E_BUDGET = -5
+CORR_E_CUDA = -6
+CORR_E_TIMEOUT = -7
+CORR_E_UNSUPPORTED = -8
+
+PATH_AUTO = 0
+PATH_CUDACORE = 1
+PATH_MMA_I8 = 2
+PATH_TC_FP8 = 3
+PATHS = {"auto": PATH_AUTO, "cudacore": PATH_CUDACORE, "mma_i8": PATH_MMA_I8,
+         "tc_fp8": PATH_TC_FP8}
+PATH_NAMES = {v: k for k, v in PATHS.items()}
+
+ZERO_INVALID = 1
+
+
+K_UNPACK, K_XENGINE, K_DUMP, K_OTHER = 0, 1, 2, 3
+KIND_NAMES = ["unpack", "xengine", "dump", "other"]
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_longlong * 4), ("timed", ctypes.c_longlong * 4),
+                ("ms", ctypes.c_double * 4)]
+
+    def as_dict(self) -> dict:
+        return {KIND_NAMES[k]: {"launches": int(self.launches[k]), "timed": int(self.timed[k]),
+                                "ms": float(self.ms[k])} for k in range(4)}
+
+
+class CorrError(RuntimeError):
+    def __init__(self, status: int, what: str):
+        self.status = status
+        super().__init__(f"{what}: {strerror(status)} ({status})")
+
+
+_lock = threading.Lock()
+_lib = None
+
+
+def library_path() -> str:
+    return _build.LIB_PATH
+
+
+def load(build_if_missing: bool = True) -> ctypes.CDLL:
+    """Load libcorr.so (building it first if it is missing and allowed)."""
+    global _lib
+    with _lock:
+        if _lib is not None:
+            return _lib
+        path = _build.LIB_PATH
+        if not os.path.exists(path):
+            if not build_if_missing:
+                raise RuntimeError(f"{path} is not built; run paper_1501_05992_gb300.build.build()")
+            _build.build()
+        lib = ctypes.CDLL(path)
+        vp, c_int, c_size = ctypes.c_void_p, ctypes.c_int, ctypes.c_size_t
+        sig = {
+            "corr_create": ([c_int, c_int, c_int], vp),
+            "corr_destroy": ([vp], c_int),
+            "corr_set_path": ([vp, c_int], c_int),
+            "corr_get_path": ([vp], c_int),
+            "corr_set_flags": ([vp, ctypes.c_uint], c_int),
+            "corr_workspace_bytes": ([vp], c_size),
+            "corr_bind_workspace": ([vp, vp, c_size], c_int),
+            "corr_accumulate": ([vp, vp, c_int, vp], c_int),
+            "corr_dump": ([vp, vp, vp], c_int),
+            "corr_samples": ([vp], ctypes.c_longlong),
+            "corr_accumulate_host": ([vp, vp, c_int, vp], c_int),
+            "corr_dump_host": ([vp, vp, vp], c_int),
+            "corr_sync": ([vp, vp], c_int),
+            "corr_state_bytes": ([vp], c_size),
+            "corr_get_state": ([vp, vp, c_size, vp], c_int),
+            "corr_set_state": ([vp, vp, c_size, vp], c_int),
+            "corr_unpack": ([vp, c_int, c_int, c_int, vp, ctypes.c_uint, vp], c_int),
+            "corr_profile_enable": ([vp, c_int], c_int),
+            "corr_profile_read": ([vp, ctypes.POINTER(Profile), c_int], c_int),
+            "corr_last_error": ([], c_int),
+            "corr_strerror": ([c_int], ctypes.c_char_p),
+            "corr_version": ([], c_int),
+        }
+        for name, (args, res) in sig.items():
+            fn = getattr(lib, name)
+            fn.argtypes = args
+            fn.restype = res
+        _lib = lib
+        return lib
+
+
+def strerror(status: int) -> str:
+    try:
+        return load().corr_strerror(int(status)).decode()
+    except Exception:  # library not loadable: still give a message
+        return f"status {status}"
+
+
+def _check(status: int, what: str) -> None:
+    if status != CORR_OK:
+        raise CorrError(status, what)
+
+
+def _stream_handle(stream) -> int | None:
+    if stream is None:
+        stream = torch.cuda.current_stream()
+    return ctypes.c_void_p(stream.cuda_stream)
+
+
+def n_pairs(n_inputs: int) -> int:
+    return n_inputs * (n_inputs + 1) // 2
+
+
+class Correlator:
+    """One X-engine context: accumulators for n_chan x N(N+1)/2 visibilities.
+
+    accumulate(volt) adds a block of uint8 [T][F][N] voltages to the running
+    integration; dump() returns (or writes) the int32 [F][P][2] packed lower
+    triangle and starts a new integration.
+    """
+
+    def __init__(self, n_inputs: int, n_chan: int, n_time_per_int: int,
+                 path: str | int = "auto", zero_invalid: bool = False,
+                 device: torch.device | int | None = None):
+        self._lib = load()
+        self.n_inputs, self.n_chan, self.n_time_per_int = n_inputs, n_chan, n_time_per_int
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   (device if isinstance(device, int) else device.index or 0))
+        with torch.cuda.device(self.device):
+            ctx = self._lib.corr_create(n_inputs, n_chan, n_time_per_int)
+            if not ctx:
+                raise CorrError(self._lib.corr_last_error(), "corr_create")
+            self._ctx = ctypes.c_void_p(ctx)
+            try:
+                if zero_invalid:
+                    _check(self._lib.corr_set_flags(self._ctx, ZERO_INVALID), "corr_set_flags")
+                self.set_path(path)
+                nbytes = self._lib.corr_workspace_bytes(self._ctx)
+                self._ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.device)
+                _check(self._lib.corr_bind_workspace(self._ctx, ctypes.c_void_p(self._ws.data_ptr()),
+                                                     nbytes), "corr_bind_workspace")
+            except Exception:
+                self._lib.corr_destroy(self._ctx)
+                self._ctx = None
+                raise
+
+    # -- properties -------------------------------------------------------
+    @property
+    def n_pairs(self) -> int:
+        return n_pairs(self.n_inputs)
+
+    @property
+    def workspace_bytes(self) -> int:
+        return int(self._ws.numel())
+
+    @property
+    def samples(self) -> int:
+        return int(self._lib.corr_samples(self._ctx))
+
+    @property
+    def path(self) -> str:
+        return PATH_NAMES[self._lib.corr_get_path(self._ctx)]
+
+    def set_path(self, path: str | int) -> None:
+        code = PATHS[path] if isinstance(path, str) else int(path)
+        _check(self._lib.corr_set_path(self._ctx, code), f"corr_set_path({path})")
+
+    # -- integration -------------------------------------------------------
+    def _check_volt(self, volt: torch.Tensor, device: bool) -> int:
+        if volt.dtype != torch.uint8 or volt.dim() != 3 or not volt.is_contiguous():
+            raise ValueError("volt must be a contiguous uint8 tensor [T][F][N]")
+        if volt.shape[1] != self.n_chan or volt.shape[2] != self.n_inputs:
+            raise ValueError(f"volt shape {tuple(volt.shape)} does not match "
+                             f"[T][{self.n_chan}][{self.n_inputs}]")
+        if device and volt.device != self.device:
+            raise ValueError(f"volt must be on {self.device}")
+        if not device and volt.device.type != "cpu":
+            raise ValueError("volt must be a host tensor")
+        return int(volt.shape[0])
+
+    def accumulate(self, volt: torch.Tensor, stream=None) -> None:
+        nt = self._check_volt(volt, device=True)
+        _check(self._lib.corr_accumulate(self._ctx, ctypes.c_void_p(volt.data_ptr()), nt,
+                                         _stream_handle(stream)), "corr_accumulate")
+
+    def dump(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.n_chan, self.n_pairs, 2), dtype=torch.int32, device=self.device)
+        elif (out.dtype != torch.int32 or out.shape != (self.n_chan, self.n_pairs, 2)
+              or not out.is_contiguous() or out.device != self.device):
+            raise ValueError("out must be a contiguous int32 [F][P][2] tensor on the device")
+        _check(self._lib.corr_dump(self._ctx, ctypes.c_void_p(out.data_ptr()),
+                                   _stream_handle(stream)), "corr_dump")
+        return out
+
+    def accumulate_host(self, volt: torch.Tensor, stream=None) -> None:
+        nt = self._check_volt(volt, device=False)
+        _check(self._lib.corr_accumulate_host(self._ctx, ctypes.c_void_p(volt.data_ptr()), nt,
+                                              _stream_handle(stream)), "corr_accumulate_host")
+
+    def dump_host(self, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        if out is None:
+            out = torch.empty((self.n_chan, self.n_pairs, 2), dtype=torch.int32, pin_memory=True)
+        elif (out.dtype != torch.int32 or out.shape != (self.n_chan, self.n_pairs, 2)
+              or not out.is_contiguous() or out.device.type != "cpu"):
+            raise ValueError("out must be a contiguous int32 [F][P][2] host tensor")
+        _check(self._lib.corr_dump_host(self._ctx, ctypes.c_void_p(out.data_ptr()),
+                                        _stream_handle(stream)), "corr_dump_host")
+        return out
+
+    def sync(self, stream=None) -> None:
+        _check(self._lib.corr_sync(self._ctx, _stream_handle(stream)), "corr_sync")
+
+    # -- profiling ---------------------------------------------------------
+    def profile_enable(self, on: bool = True) -> None:
+        _check(self._lib.corr_profile_enable(self._ctx, int(on)), "corr_profile_enable")
+
+    def profile_read(self, reset: bool = True) -> dict:
+        prof = Profile()
+        _check(self._lib.corr_profile_read(self._ctx, ctypes.byref(prof), int(reset)),
+               "corr_profile_read")
+        return prof.as_dict()
+
+    # -- checkpoint / resume ---------------------------------------------
+    def get_state(self, stream=None) -> bytes:
+        nb = self._lib.corr_state_bytes(self._ctx)
+        buf = ctypes.create_string_buffer(nb)
+        _check(self._lib.corr_get_state(self._ctx, buf, nb, _stream_handle(stream)),
+               "corr_get_state")
+        return buf.raw
+
+    def set_state(self, state: bytes, stream=None) -> None:
+        buf = ctypes.create_string_buffer(bytes(state), len(state))
+        _check(self._lib.corr_set_state(self._ctx, buf, len(state), _stream_handle(stream)),
+               "corr_set_state")
+
+    # -- lifetime -----------------------------------------------------------
+    def close(self) -> None:
+        if getattr(self, "_ctx", None):
+            self._lib.corr_destroy(self._ctx)
+            self._ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+
+def unpack(volt: torch.Tensor, zero_invalid: bool = False, stream=None) -> torch.Tensor:
+    """K1 on its own: uint8 [T][F][N] -> int8 [F][N][T][2] (real, imaginary)."""
+    if volt.dtype != torch.uint8 or volt.dim() != 3 or not volt.is_contiguous() or not volt.is_cuda:
+        raise ValueError("volt must be a contiguous uint8 CUDA tensor [T][F][N]")
+    T, F, N = volt.shape
+    out = torch.empty((F, N, T, 2), dtype=torch.int8, device=volt.device)
+    _check(load().corr_unpack(ctypes.c_void_p(volt.data_ptr()), T, F, N,
+                              ctypes.c_void_p(out.data_ptr()), ZERO_INVALID if zero_invalid else 0,
+                              _stream_handle(stream)), "corr_unpack")
+    return out

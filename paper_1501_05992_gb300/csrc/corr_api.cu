@@ -1,0 +1,620 @@
+// C ABI of the X-engine library: context, workspace, integration control,
+// host-buffer transfers, checkpoint/resume and errors (declared in corr.h).
+//
+// Call structure of one integration (Section 3.4.1: a block of input is
+// released to the GPU; Section 3.4.3: products accumulate on the device and
+// are copied out at the end of the operator-chosen accumulation length):
+//
+//   corr_accumulate(volt)  -> [unpack K1 ->] X-engine K2 into the int32
+//                             packed-triangle accumulators (all on `stream`)
+//   corr_dump(vis)         -> K3 copy, accumulators marked fresh
+//
+// Nothing here synchronises the host except corr_sync and the state calls.
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <new>
+#include <utility>
+#include <vector>
+
+#include "internal.cuh"
+
+using namespace corr;
+
+struct corr_ctx {
+    int n = 0, f = 0, t_max = 0;
+    int device = 0, sm_major = 0, sm_minor = 0, sm_count = 0;
+    int path = CORR_PATH_AUTO;
+    unsigned flags = 0;
+
+    // workspace (caller-owned device memory)
+    uint8_t *ws = nullptr;
+    size_t ws_bytes = 0;
+    DeviceStatus *status = nullptr;
+    int32_t *acc = nullptr;
+    uint8_t *stage = nullptr;
+    uint8_t *host_stage[2] = {nullptr, nullptr};
+
+    StagePlan dp4a{}, mma{};
+    int host_chunk = 0;
+
+    long long samples = 0;
+    bool fresh = true;     // accumulators hold no data: next X-engine stores
+
+    cudaStream_t copy_stream = nullptr;
+    cudaEvent_t ev_full[2] = {nullptr, nullptr};
+    cudaEvent_t ev_free[2] = {nullptr, nullptr};
+
+    // profiling: launch counts (always) and event pairs (when enabled)
+    bool prof_on = false;
+    long long prof_launches[CORR_K_KINDS] = {0, 0, 0, 0};
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pending[CORR_K_KINDS];
+    std::vector<std::pair<cudaEvent_t, cudaEvent_t>> prof_pool;
+    std::pair<cudaEvent_t, cudaEvent_t> prof_cur{nullptr, nullptr};
+};
+
+namespace {
+
+thread_local int g_last_error = CORR_OK;
+
+int ret(int status)
+{
+    g_last_error = status;
+    return status;
+}
+
+struct WsLayout {
+    size_t status_off, acc_off, stage_off, host_off[2], total;
+};
+
+size_t acc_words(const corr_ctx *c) { return size_t(c->f) * size_t(n_pairs(c->n)) * 2; }
+
+WsLayout layout_of(const corr_ctx *c)
+{
+    WsLayout L{};
+    size_t off = 0;
+    L.status_off = off;
+    off = round_up(off + sizeof(DeviceStatus), kAlign);
+    L.acc_off = off;
+    off = round_up(off + acc_words(c) * sizeof(int32_t), kAlign);
+    L.stage_off = off;
+    const size_t stage = c->dp4a.bytes > c->mma.bytes ? c->dp4a.bytes : c->mma.bytes;
+    off = round_up(off + stage, kAlign);
+    const size_t host = size_t(c->host_chunk) * size_t(c->f) * size_t(c->n);
+    for (int b = 0; b < 2; ++b) {
+        L.host_off[b] = off;
+        off = round_up(off + host, kAlign);
+    }
+    L.total = off;
+    return L;
+}
+
+int resolve_path(const corr_ctx *c, int requested)
+{
+    if (requested != CORR_PATH_AUTO) return requested;
+    if (tc_supported(c->n, c->device) && c->n >= 64) return CORR_PATH_TC_FP8;
+    return CORR_PATH_CUDACORE;
+}
+
+bool path_supported(const corr_ctx *c, int path)
+{
+    switch (path) {
+    case CORR_PATH_AUTO:
+    case CORR_PATH_CUDACORE:
+    case CORR_PATH_MMA_I8:
+        return true;
+    case CORR_PATH_TC_FP8:
+        return tc_supported(c->n, c->device);
+    default:
+        return false;
+    }
+}
+
+int cuda_fail(cudaError_t e)
+{
+    (void)e;
+    return CORR_E_CUDA;
+}
+
+// Bracket a launch with timing events when profiling is on.
+void prof_begin(corr_ctx *c, cudaStream_t s)
+{
+    if (!c->prof_on) return;
+    std::pair<cudaEvent_t, cudaEvent_t> ev{nullptr, nullptr};
+    if (!c->prof_pool.empty()) {
+        ev = c->prof_pool.back();
+        c->prof_pool.pop_back();
+    } else if (cudaEventCreate(&ev.first) != cudaSuccess ||
+               cudaEventCreate(&ev.second) != cudaSuccess) {
+        cudaGetLastError();
+        c->prof_cur = {nullptr, nullptr};
+        return;
+    }
+    cudaEventRecord(ev.first, s);
+    c->prof_cur = ev;
+}
+
+void prof_end(corr_ctx *c, int kind, cudaStream_t s, int launches)
+{
+    c->prof_launches[kind] += launches;
+    if (!c->prof_on || !c->prof_cur.first) return;
+    cudaEventRecord(c->prof_cur.second, s);
+    c->prof_pending[kind].push_back(c->prof_cur);
+    c->prof_cur = {nullptr, nullptr};
+}
+
+// Correlate n_time samples already in device memory.
+int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
+{
+    const int path = resolve_path(c, c->path);
+    const bool zi = (c->flags & CORR_ZERO_INVALID) != 0;
+    bool fresh = c->fresh;
+    cudaError_t e = cudaSuccess;
+    const size_t row = size_t(c->f) * size_t(c->n);
+    if (path == CORR_PATH_TC_FP8) {
+        prof_begin(c, s);
+        e = launch_xeng_tc(volt, c->f, c->n, nt, zi, c->acc, fresh, c->status, s);
+        prof_end(c, CORR_K_XENGINE, s, 1);
+        if (e != cudaSuccess) return cuda_fail(e);
+    } else if (path == CORR_PATH_CUDACORE) {
+        const StagePlan &P = c->dp4a;
+        const size_t plane_max = size_t(P.f_chunk) * (P.t_chunk / 2) * P.n_pad;
+        int32_t *A = reinterpret_cast<int32_t *>(c->stage);
+        int32_t *W = A + plane_max;
+        for (int t0 = 0; t0 < nt; t0 += P.t_chunk) {
+            const int ntc = nt - t0 < P.t_chunk ? nt - t0 : P.t_chunk;
+            const int tw_pad = int(round_up(size_t(ntc), 2 * kDp4aKW) / 2);
+            for (int f0 = 0; f0 < c->f; f0 += P.f_chunk) {
+                const int fc = c->f - f0 < P.f_chunk ? c->f - f0 : P.f_chunk;
+                prof_begin(c, s);
+                e = launch_unpack_words(volt + size_t(t0) * row, c->f, c->n, f0, fc, ntc, P.n_pad,
+                                        tw_pad, zi, A, W, s);
+                prof_end(c, CORR_K_UNPACK, s, 1);
+                if (e != cudaSuccess) return cuda_fail(e);
+                prof_begin(c, s);
+                e = launch_xeng_dp4a(A, W, c->n, P.n_pad, fc, tw_pad, c->acc, f0, fresh, s);
+                prof_end(c, CORR_K_XENGINE, s, 1);
+                if (e != cudaSuccess) return cuda_fail(e);
+            }
+            fresh = false;
+        }
+    } else if (path == CORR_PATH_MMA_I8) {
+        const StagePlan &P = c->mma;
+        const size_t plane_max = size_t(P.f_chunk) * P.t_chunk * 2 * P.n_pad;
+        int8_t *X = reinterpret_cast<int8_t *>(c->stage);
+        int8_t *Xt = X + plane_max;
+        for (int t0 = 0; t0 < nt; t0 += P.t_chunk) {
+            const int ntc = nt - t0 < P.t_chunk ? nt - t0 : P.t_chunk;
+            const int t_pad = int(round_up(size_t(ntc), kMmaKT));
+            for (int f0 = 0; f0 < c->f; f0 += P.f_chunk) {
+                const int fc = c->f - f0 < P.f_chunk ? c->f - f0 : P.f_chunk;
+                prof_begin(c, s);
+                e = launch_unpack_kmajor(volt + size_t(t0) * row, c->f, c->n, f0, fc, ntc, P.n_pad,
+                                         t_pad, zi, X, Xt, s);
+                prof_end(c, CORR_K_UNPACK, s, 1);
+                if (e != cudaSuccess) return cuda_fail(e);
+                prof_begin(c, s);
+                e = launch_xeng_mma8(X, Xt, c->n, P.n_pad, fc, t_pad, c->acc, f0, fresh, s);
+                prof_end(c, CORR_K_XENGINE, s, 1);
+                if (e != cudaSuccess) return cuda_fail(e);
+            }
+            fresh = false;
+        }
+    } else {
+        return CORR_E_UNSUPPORTED;
+    }
+    c->fresh = false;
+    return CORR_OK;
+}
+
+}  // namespace
+
+namespace corr {
+
+StagePlan plan_dp4a(int n_inputs, int n_chan, int t_max)
+{
+    StagePlan P{};
+    P.n_pad = int(round_up(size_t(n_inputs), kDp4aTile));
+    size_t t_chunk = round_up(size_t(t_max), 2 * kDp4aKW);
+    if (t_chunk > 8192) t_chunk = 8192;
+    // two int32 planes of t_chunk/2 words per input: 4 * t_chunk * n_pad bytes/channel
+    while (t_chunk > size_t(2 * kDp4aKW) && 4 * t_chunk * P.n_pad > kStageCap)
+        t_chunk -= 2 * kDp4aKW;
+    const size_t per_chan = 4 * t_chunk * P.n_pad;
+    size_t fc = kStageCap / per_chan;
+    if (fc < 1) fc = 1;
+    if (fc > size_t(n_chan)) fc = size_t(n_chan);
+    if (fc > 65535) fc = 65535;
+    P.t_chunk = int(t_chunk);
+    P.f_chunk = int(fc);
+    P.bytes = per_chan * fc;
+    return P;
+}
+
+StagePlan plan_mma(int n_inputs, int n_chan, int t_max)
+{
+    StagePlan P{};
+    P.n_pad = int(round_up(size_t(n_inputs), kMmaTile));
+    size_t t_chunk = round_up(size_t(t_max), kMmaKT);
+    if (t_chunk > 8192) t_chunk = 8192;
+    // two int8 planes (X and twisted) of 2 bytes per sample: 4 * t_chunk * n_pad bytes/channel
+    while (t_chunk > size_t(kMmaKT) && 4 * t_chunk * P.n_pad > kStageCap) t_chunk -= kMmaKT;
+    const size_t per_chan = 4 * t_chunk * P.n_pad;
+    size_t fc = kStageCap / per_chan;
+    if (fc < 1) fc = 1;
+    if (fc > size_t(n_chan)) fc = size_t(n_chan);
+    if (fc > 65535) fc = 65535;
+    P.t_chunk = int(t_chunk);
+    P.f_chunk = int(fc);
+    P.bytes = per_chan * fc;
+    return P;
+}
+
+}  // namespace corr
+
+extern "C" {
+
+corr_ctx *corr_create(int n_inputs, int n_chan, int n_time_per_int)
+{
+    if (n_inputs < 1 || n_chan < 1 || n_time_per_int < 1 || n_inputs > 8192 ||
+        (long long)n_time_per_int * 128LL >= (1LL << 31)) {
+        ret(CORR_E_ARG);
+        return nullptr;
+    }
+    corr_ctx *c = new (std::nothrow) corr_ctx();
+    if (!c) {
+        ret(CORR_E_NOMEM);
+        return nullptr;
+    }
+    c->n = n_inputs;
+    c->f = n_chan;
+    c->t_max = n_time_per_int;
+    cudaDeviceProp prop;
+    if (cudaGetDevice(&c->device) != cudaSuccess ||
+        cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        ret(CORR_E_CUDA);
+        return nullptr;
+    }
+    c->sm_major = prop.major;
+    c->sm_minor = prop.minor;
+    c->sm_count = prop.multiProcessorCount;
+    c->dp4a = plan_dp4a(n_inputs, n_chan, n_time_per_int);
+    c->mma = plan_mma(n_inputs, n_chan, n_time_per_int);
+    c->host_chunk = n_time_per_int < kHostChunk ? n_time_per_int : kHostChunk;
+    if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+        cudaGetLastError();
+        delete c;
+        ret(CORR_E_CUDA);
+        return nullptr;
+    }
+    for (int b = 0; b < 2; ++b) {
+        if (cudaEventCreateWithFlags(&c->ev_full[b], cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&c->ev_free[b], cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            corr_destroy(c);
+            ret(CORR_E_CUDA);
+            return nullptr;
+        }
+    }
+    ret(CORR_OK);
+    return c;
+}
+
+int corr_destroy(corr_ctx *c)
+{
+    if (!c) return ret(CORR_E_ARG);
+    for (int b = 0; b < 2; ++b) {
+        if (c->ev_full[b]) cudaEventDestroy(c->ev_full[b]);
+        if (c->ev_free[b]) cudaEventDestroy(c->ev_free[b]);
+    }
+    if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    for (int k = 0; k < CORR_K_KINDS; ++k)
+        for (auto &ev : c->prof_pending[k]) c->prof_pool.push_back(ev);
+    for (auto &ev : c->prof_pool) {
+        cudaEventDestroy(ev.first);
+        cudaEventDestroy(ev.second);
+    }
+    delete c;
+    return ret(CORR_OK);
+}
+
+int corr_set_path(corr_ctx *c, int path)
+{
+    if (!c || path < CORR_PATH_AUTO || path > CORR_PATH_TC_FP8) return ret(CORR_E_ARG);
+    if (c->samples != 0) return ret(CORR_E_STATE);
+    if (!path_supported(c, path)) return ret(CORR_E_UNSUPPORTED);
+    c->path = path;
+    return ret(CORR_OK);
+}
+
+int corr_get_path(const corr_ctx *c)
+{
+    if (!c) return ret(CORR_E_ARG);
+    g_last_error = CORR_OK;
+    return resolve_path(c, c->path);
+}
+
+int corr_set_flags(corr_ctx *c, unsigned flags)
+{
+    if (!c || (flags & ~CORR_ZERO_INVALID)) return ret(CORR_E_ARG);
+    if (c->samples != 0) return ret(CORR_E_STATE);
+    c->flags = flags;
+    return ret(CORR_OK);
+}
+
+size_t corr_workspace_bytes(const corr_ctx *c)
+{
+    if (!c) {
+        ret(CORR_E_ARG);
+        return 0;
+    }
+    g_last_error = CORR_OK;
+    return layout_of(c).total;
+}
+
+int corr_bind_workspace(corr_ctx *c, void *d_ws, size_t bytes)
+{
+    if (!c || !d_ws || (reinterpret_cast<uintptr_t>(d_ws) % kAlign) != 0) return ret(CORR_E_ARG);
+    const WsLayout L = layout_of(c);
+    if (bytes < L.total) return ret(CORR_E_ARG);
+    c->ws = static_cast<uint8_t *>(d_ws);
+    c->ws_bytes = bytes;
+    c->status = reinterpret_cast<DeviceStatus *>(c->ws + L.status_off);
+    c->acc = reinterpret_cast<int32_t *>(c->ws + L.acc_off);
+    c->stage = c->ws + L.stage_off;
+    c->host_stage[0] = c->ws + L.host_off[0];
+    c->host_stage[1] = c->ws + L.host_off[1];
+    c->samples = 0;
+    c->fresh = true;
+    if (cudaMemset(c->status, 0, sizeof(DeviceStatus)) != cudaSuccess) {
+        cudaGetLastError();
+        return ret(CORR_E_CUDA);
+    }
+    return ret(CORR_OK);
+}
+
+int corr_accumulate(corr_ctx *c, const uint8_t *d_volt, int n_time, void *stream)
+{
+    if (!c || n_time < 0) return ret(CORR_E_ARG);
+    if (!c->ws) return ret(CORR_E_STATE);
+    if (n_time == 0) return ret(CORR_OK);
+    if (!d_volt) return ret(CORR_E_ARG);
+    if (c->samples + n_time > c->t_max) return ret(CORR_E_OVERFLOW);
+    const int rc = accumulate_device(c, d_volt, n_time, static_cast<cudaStream_t>(stream));
+    if (rc != CORR_OK) return ret(rc);
+    c->samples += n_time;
+    return ret(CORR_OK);
+}
+
+int corr_dump(corr_ctx *c, int32_t *d_vis, void *stream)
+{
+    if (!c || !d_vis) return ret(CORR_E_ARG);
+    if (!c->ws) return ret(CORR_E_STATE);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    int launches = 0;
+    prof_begin(c, s);
+    cudaError_t e = launch_dump(c->acc, d_vis, acc_words(c), c->fresh, s, &launches);
+    prof_end(c, CORR_K_DUMP, s, launches);
+    if (e != cudaSuccess) return ret(cuda_fail(e));
+    c->fresh = true;
+    c->samples = 0;
+    return ret(CORR_OK);
+}
+
+long long corr_samples(const corr_ctx *c)
+{
+    if (!c) {
+        ret(CORR_E_ARG);
+        return -1;
+    }
+    g_last_error = CORR_OK;
+    return c->samples;
+}
+
+int corr_accumulate_host(corr_ctx *c, const uint8_t *h_volt, int n_time, void *stream)
+{
+    if (!c || n_time < 0) return ret(CORR_E_ARG);
+    if (!c->ws) return ret(CORR_E_STATE);
+    if (n_time == 0) return ret(CORR_OK);
+    if (!h_volt) return ret(CORR_E_ARG);
+    if (c->samples + n_time > c->t_max) return ret(CORR_E_OVERFLOW);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t row = size_t(c->f) * size_t(c->n);
+    int k = 0;
+    for (int t0 = 0; t0 < n_time; t0 += c->host_chunk, ++k) {
+        const int ntc = n_time - t0 < c->host_chunk ? n_time - t0 : c->host_chunk;
+        const int b = k & 1;
+        if (cudaStreamWaitEvent(c->copy_stream, c->ev_free[b], 0) != cudaSuccess ||
+            cudaMemcpyAsync(c->host_stage[b], h_volt + size_t(t0) * row, size_t(ntc) * row,
+                            cudaMemcpyHostToDevice, c->copy_stream) != cudaSuccess ||
+            cudaEventRecord(c->ev_full[b], c->copy_stream) != cudaSuccess ||
+            cudaStreamWaitEvent(s, c->ev_full[b], 0) != cudaSuccess) {
+            cudaGetLastError();
+            return ret(CORR_E_CUDA);
+        }
+        const int rc = accumulate_device(c, c->host_stage[b], ntc, s);
+        if (rc != CORR_OK) return ret(rc);
+        c->samples += ntc;
+        if (cudaEventRecord(c->ev_free[b], s) != cudaSuccess) {
+            cudaGetLastError();
+            return ret(CORR_E_CUDA);
+        }
+    }
+    return ret(CORR_OK);
+}
+
+int corr_dump_host(corr_ctx *c, int32_t *h_vis, void *stream)
+{
+    if (!c || !h_vis) return ret(CORR_E_ARG);
+    if (!c->ws) return ret(CORR_E_STATE);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const size_t bytes = acc_words(c) * sizeof(int32_t);
+    if (c->fresh && cudaMemsetAsync(c->acc, 0, bytes, s) != cudaSuccess) {
+        cudaGetLastError();
+        return ret(CORR_E_CUDA);
+    }
+    if (cudaMemcpyAsync(h_vis, c->acc, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+        cudaGetLastError();
+        return ret(CORR_E_CUDA);
+    }
+    c->fresh = true;
+    c->samples = 0;
+    return ret(CORR_OK);
+}
+
+int corr_sync(corr_ctx *c, void *stream)
+{
+    if (!c) return ret(CORR_E_ARG);
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+        cudaGetLastError();
+        return ret(CORR_E_CUDA);
+    }
+    if (!c->status) return ret(CORR_OK);
+    DeviceStatus st{};
+    if (cudaMemcpy(&st, c->status, sizeof(st), cudaMemcpyDeviceToHost) != cudaSuccess) {
+        cudaGetLastError();
+        return ret(CORR_E_CUDA);
+    }
+    if (st.code != 0) {
+        cudaMemset(c->status, 0, sizeof(DeviceStatus));
+        return ret(st.code);
+    }
+    return ret(CORR_OK);
+}
+
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t n, f;
+    int64_t samples;
+    int64_t reserved;
+};
+static_assert(sizeof(StateHeader) == 32, "state header is 32 bytes");
+static const uint32_t kStateMagic = 0x52524F43u;  // "CORR"
+
+size_t corr_state_bytes(const corr_ctx *c)
+{
+    if (!c) {
+        ret(CORR_E_ARG);
+        return 0;
+    }
+    g_last_error = CORR_OK;
+    return sizeof(StateHeader) + acc_words(c) * sizeof(int32_t);
+}
+
+int corr_get_state(corr_ctx *c, void *h_buf, size_t bytes, void *stream)
+{
+    if (!c || !h_buf || bytes < corr_state_bytes(c)) return ret(CORR_E_ARG);
+    if (!c->ws) return ret(CORR_E_STATE);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    StateHeader h{kStateMagic, 1u, c->n, c->f, c->samples, 0};
+    std::memcpy(h_buf, &h, sizeof(h));
+    uint8_t *dst = static_cast<uint8_t *>(h_buf) + sizeof(h);
+    const size_t nb = acc_words(c) * sizeof(int32_t);
+    if (c->fresh) {
+        std::memset(dst, 0, nb);
+        if (cudaStreamSynchronize(s) != cudaSuccess) {
+            cudaGetLastError();
+            return ret(CORR_E_CUDA);
+        }
+        return ret(CORR_OK);
+    }
+    if (cudaMemcpyAsync(dst, c->acc, nb, cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return ret(CORR_E_CUDA);
+    }
+    return ret(CORR_OK);
+}
+
+int corr_set_state(corr_ctx *c, const void *h_buf, size_t bytes, void *stream)
+{
+    if (!c || !h_buf || bytes < corr_state_bytes(c)) return ret(CORR_E_ARG);
+    if (!c->ws) return ret(CORR_E_STATE);
+    StateHeader h;
+    std::memcpy(&h, h_buf, sizeof(h));
+    if (h.magic != kStateMagic || h.version != 1u || h.n != c->n || h.f != c->f ||
+        h.samples < 0 || h.samples > c->t_max)
+        return ret(CORR_E_ARG);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const uint8_t *src = static_cast<const uint8_t *>(h_buf) + sizeof(h);
+    const size_t nb = acc_words(c) * sizeof(int32_t);
+    if (cudaMemcpyAsync(c->acc, src, nb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
+        cudaStreamSynchronize(s) != cudaSuccess) {
+        cudaGetLastError();
+        return ret(CORR_E_CUDA);
+    }
+    c->samples = h.samples;
+    c->fresh = false;
+    return ret(CORR_OK);
+}
+
+int corr_unpack(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs, int8_t *d_out,
+                unsigned flags, void *stream)
+{
+    if (n_time < 0 || n_chan < 1 || n_inputs < 1 || n_chan > 65535 ||
+        (flags & ~CORR_ZERO_INVALID))
+        return ret(CORR_E_ARG);
+    if (n_time == 0) return ret(CORR_OK);
+    if (!d_volt || !d_out) return ret(CORR_E_ARG);
+    cudaError_t e = launch_unpack_kmajor(d_volt, n_chan, n_inputs, 0, n_chan, n_time, n_inputs,
+                                         n_time, (flags & CORR_ZERO_INVALID) != 0, d_out,
+                                         nullptr, static_cast<cudaStream_t>(stream));
+    return ret(e == cudaSuccess ? CORR_OK : CORR_E_CUDA);
+}
+
+int corr_profile_enable(corr_ctx *c, int on)
+{
+    if (!c) return ret(CORR_E_ARG);
+    c->prof_on = on != 0;
+    return ret(CORR_OK);
+}
+
+int corr_profile_read(corr_ctx *c, corr_profile *out, int reset)
+{
+    if (!c || !out) return ret(CORR_E_ARG);
+    for (int k = 0; k < CORR_K_KINDS; ++k) {
+        double ms = 0.0;
+        for (auto &ev : c->prof_pending[k]) {
+            float t = 0.f;
+            if (cudaEventSynchronize(ev.second) != cudaSuccess ||
+                cudaEventElapsedTime(&t, ev.first, ev.second) != cudaSuccess) {
+                cudaGetLastError();
+                return ret(CORR_E_CUDA);
+            }
+            ms += t;
+        }
+        out->launches[k] = c->prof_launches[k];
+        out->timed[k] = (long long)c->prof_pending[k].size();
+        out->ms[k] = ms;
+        if (reset) {
+            for (auto &ev : c->prof_pending[k]) c->prof_pool.push_back(ev);
+            c->prof_pending[k].clear();
+            c->prof_launches[k] = 0;
+        }
+    }
+    return ret(CORR_OK);
+}
+
+int corr_last_error(void) { return g_last_error; }
+
+const char *corr_strerror(int status)
+{
+    switch (status) {
+    case CORR_OK: return "success";
+    case CORR_E_ARG: return "invalid argument";
+    case CORR_E_STATE: return "call not valid in the current state";
+    case CORR_E_OVERFLOW: return "integration would exceed n_time_per_int";
+    case CORR_E_NOMEM: return "out of memory";
+    case CORR_E_BUDGET: return "memory budget exceeded";
+    case CORR_E_CUDA: return "CUDA runtime error";
+    case CORR_E_TIMEOUT: return "device-side wait timed out";
+    case CORR_E_UNSUPPORTED: return "unsupported shape or path on this device";
+    default: return "unknown status";
+    }
+}
+
+int corr_version(void) { return 100; }
+
+}  // extern "C"

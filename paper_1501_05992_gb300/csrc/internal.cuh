@@ -1,0 +1,86 @@
+// Internal declarations shared by the translation units of libcorr.so.
+// Not part of the public ABI (that is include/corr.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+#include <stdint.h>
+
+#include "corr.h"
+
+namespace corr {
+
+// ----------------------------------------------------------------- sizes ---
+constexpr int kDp4aTile = 64;          // CUDA-core X-engine tile (inputs per side)
+constexpr int kDp4aKW = 32;            // 32-bit words (2 samples each) per K stage
+constexpr int kMmaTile = 64;           // int8 mma.sync tile (inputs per side)
+constexpr int kMmaKT = 64;             // samples per K stage of the mma.sync kernel
+constexpr size_t kStageCap = size_t(1) << 30;  // unpacked-operand staging cap, bytes
+constexpr int kHostChunk = 500;        // samples per host->device transfer chunk
+constexpr size_t kAlign = 256;
+
+__host__ __device__ inline long long n_pairs(long long n) { return n * (n + 1) / 2; }
+inline size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+inline int div_up(int a, int b) { return (a + b - 1) / b; }
+
+// Device status words written by kernels (index 0: error code, 1..3: detail).
+struct DeviceStatus {
+    int code;
+    int where;
+    int detail0;
+    int detail1;
+};
+
+// Plan for the unpacked-operand paths (CUDA-core and mma.sync): the call's
+// samples are processed in time chunks of t_chunk samples and channel chunks
+// of f_chunk channels, each unpacked into the staging buffer then correlated.
+struct StagePlan {
+    int n_pad;        // inputs padded to the tile
+    int t_chunk;      // samples per time chunk (even, multiple of the K stage)
+    int f_chunk;      // channels per channel chunk
+    size_t bytes;     // staging bytes needed
+};
+
+StagePlan plan_dp4a(int n_inputs, int n_chan, int t_max);
+StagePlan plan_mma(int n_inputs, int n_chan, int t_max);
+
+// ------------------------------------------------------------- launchers ---
+// All launchers enqueue on `s` and return cudaGetLastError().
+
+// Unpack channel chunk [f0, f0+fc) of samples [0, nt) of volt (uint8
+// [*][n_chan][n] with row stride n_chan*n) into the dp4a operand planes:
+// A[fc][tw_pad][n_pad] and W[fc][tw_pad][n_pad] (int8x4 words, two samples
+// per word: (r0, m0, r1, m1) and (-m0, r0, -m1, r1)); zero beyond nt / n.
+cudaError_t launch_unpack_words(const uint8_t *volt, int n_chan, int n, int f0, int fc,
+                                int nt, int n_pad, int tw_pad, bool zero_invalid,
+                                int32_t *A, int32_t *W, cudaStream_t s);
+
+// Unpack into the K-major int8 layout out[fc][n_pad][t_pad][2] (real, imag),
+// zero beyond nt / n; if out_tw is not NULL also the twisted plane (-m, r).
+// Also used by corr_unpack with n_pad = n, t_pad = nt, out_tw = NULL.
+cudaError_t launch_unpack_kmajor(const uint8_t *volt, int n_chan, int n, int f0, int fc,
+                                 int nt, int n_pad, int t_pad, bool zero_invalid,
+                                 int8_t *out, int8_t *out_tw, cudaStream_t s);
+
+// CUDA-core X-engine over a staged channel chunk; adds (or, if `fresh`,
+// stores) into acc[f0 + fl][P][2].
+cudaError_t launch_xeng_dp4a(const int32_t *A, const int32_t *W, int n, int n_pad, int fc,
+                             int tw_pad, int32_t *acc, int f0, bool fresh, cudaStream_t s);
+
+// int8 mma.sync X-engine over a staged K-major channel chunk (X and its
+// twisted plane Xt, both [fc][n_pad][t_pad][2]).
+cudaError_t launch_xeng_mma8(const int8_t *X, const int8_t *Xt, int n, int n_pad, int fc,
+                             int t_pad, int32_t *acc, int f0, bool fresh, cudaStream_t s);
+
+// tcgen05 FP8 X-engine straight from packed voltages (no staging).
+struct TcPlan;
+bool tc_supported(int n_inputs, int device);
+cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool zero_invalid,
+                           int32_t *acc, bool fresh, DeviceStatus *status, cudaStream_t s);
+
+// Dump: vis = acc (or zeros if `fresh`), n_words int32 words.  *launches
+// receives the number of kernels enqueued.
+cudaError_t launch_dump(const int32_t *acc, int32_t *vis, size_t n_words, bool fresh,
+                        cudaStream_t s, int *launches);
+
+}  // namespace corr

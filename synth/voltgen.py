@@ -55,7 +55,7 @@ CHANNEL_WIDTH_HZ = 1.0e4      # 10 kHz fine channels (Section 3.2.1)
 TAU_MAX_S = 2.0e-6            # seeded delays drawn uniformly in [-TAU_MAX, TAU_MAX]
 TONE_CYCLES_PER_SAMPLE = 0.0123
 
-# Irwin-Hall(4) of bytes: sum of four uniforms on 0..255 minus 512
+# Irwin-Hall(4) of bytes: sum of four uniforms on 0..255 minus 510 (mean 0)
 _IH4_SIGMA = math.sqrt(4.0 * (256.0 ** 2 - 1.0) / 12.0)
 
 
@@ -90,14 +90,14 @@ def hash_idx(key: int, idx: np.ndarray) -> np.ndarray:
 
 
 def _ih4_pair(h: np.ndarray):
-    """Irwin-Hall(4) pair from one hash: (sum of bytes 0..3) - 512 and
-    (sum of bytes 4..7) - 512, as int32 arrays (bytes in little-endian order
+    """Irwin-Hall(4) pair from one hash: (sum of bytes 0..3) - 510 and
+    (sum of bytes 4..7) - 510 (zero mean), as int32 arrays (bytes in little-endian order
     of the 64-bit value)."""
     h = np.ascontiguousarray(h, dtype=np.uint64)
     b = h.view(np.uint8).reshape(h.shape + (2, 4))
     if not np.little_endian:          # keep byte k = bits 8k..8k+7
         b = b[..., ::-1, ::-1]
-    s = b.sum(axis=-1, dtype=np.int32) - 512
+    s = b.sum(axis=-1, dtype=np.int32) - 510
     return s[..., 0], s[..., 1]
 
 

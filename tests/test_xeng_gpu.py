@@ -1,0 +1,198 @@
+"""Parity of every X-engine path with the CPU oracle (bit-exact: the method is
+exact integer arithmetic, so the tolerance is zero)."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from synth import voltgen as vg
+from paper_1501_05992_gb300 import corr
+
+from _gpu import ALL_PATHS, correlate, path_available
+
+pytestmark = pytest.mark.gpu
+
+
+def _paths_for(n_inputs):
+    return [p for p in ALL_PATHS if path_available(p, n_inputs)]
+
+
+@pytest.fixture(scope="module")
+def small_volt():
+    name = "small"
+    recipe, seed, arrays, _ = vg.WORKLOADS[name]
+    spec = arrays[0]
+    p = vg.make_params(recipe, seed, spec)
+    return vg.generate(p, 0, spec.n_time)
+
+
+@pytest.fixture(scope="module")
+def coarse_volt():
+    recipe, seed, arrays, _ = vg.WORKLOADS["coarse_channel"]
+    spec = arrays[0]
+    p = vg.make_params(recipe, seed, spec)
+    volt = vg.generate(p, 0, spec.n_time)
+    return volt, oracle.to_int32(oracle.xmac(volt))
+
+
+@pytest.mark.parametrize("path", ALL_PATHS)
+def test_small_workload_exact(path, small_volt):
+    if not path_available(path, small_volt.shape[2]):
+        pytest.skip(f"{path} unsupported for N={small_volt.shape[2]}")
+    want = oracle.to_int32(oracle.xmac(small_volt))
+    got = correlate(small_volt, path)
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("path", ALL_PATHS)
+def test_coarse_channel_workload_exact(path, coarse_volt):
+    volt, want = coarse_volt
+    if not path_available(path, volt.shape[2]):
+        pytest.skip(f"{path} unsupported")
+    got = correlate(volt, path)
+    assert np.array_equal(got, want)
+
+
+ODD_SHAPES = [(1, 1, 1), (2, 3, 31), (3, 2, 63), (17, 3, 65), (16, 1, 1), (32, 2, 97),
+              (64, 2, 100), (65, 2, 129), (128, 1, 255), (130, 1, 257), (144, 2, 300),
+              (192, 1, 130), (256, 1, 4097)]
+
+
+@pytest.mark.parametrize("path", ALL_PATHS)
+@pytest.mark.parametrize("shape", ODD_SHAPES, ids=lambda s: "N%d_F%d_T%d" % s)
+def test_odd_shapes_exact(path, shape):
+    N, F, T = shape
+    if not path_available(path, N):
+        pytest.skip(f"{path} unsupported for N={N}")
+    rng = np.random.default_rng(N * 1000 + F * 10 + T)
+    volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)     # every code, including 8
+    want = oracle.to_int32(oracle.xmac(volt))
+    assert np.array_equal(correlate(volt, path), want)
+
+
+@pytest.mark.parametrize("path", ALL_PATHS)
+def test_extreme_values_exact(path):
+    """All samples -8-8i (the largest magnitude), then alternating extremes."""
+    N, F, T = 64, 2, 3000
+    if not path_available(path, N):
+        pytest.skip(f"{path} unsupported")
+    volt = np.full((T, F, N), 0x88, np.uint8)
+    volt[1::2, :, ::2] = 0x77
+    volt[::3, 1, 1::2] = 0x87
+    want = oracle.to_int32(oracle.xmac(volt))
+    assert np.array_equal(correlate(volt, path), want)
+
+
+@pytest.mark.parametrize("path", ALL_PATHS)
+def test_zero_invalid_exact(path):
+    N, F, T = 48, 3, 200
+    if not path_available(path, N):
+        pytest.skip(f"{path} unsupported")
+    rng = np.random.default_rng(5)
+    volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    want = oracle.to_int32(oracle.xmac(volt, zero_invalid=True))
+    assert np.array_equal(correlate(volt, path, zero_invalid=True), want)
+
+
+@pytest.mark.parametrize("path", ALL_PATHS)
+def test_split_accumulate_and_dump_resets(path):
+    N, F, T = 96, 4, 1000
+    if not path_available(path, N):
+        pytest.skip(f"{path} unsupported")
+    rng = np.random.default_rng(7)
+    volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    want = oracle.to_int32(oracle.xmac(volt))
+    got = correlate(volt, path, chunks=[(0, 300), (300, 301), (301, 333), (333, 1000)])
+    assert np.array_equal(got, want)
+
+    c = corr.Correlator(N, F, T, path=path)
+    vt = torch.from_numpy(volt).cuda()
+    c.accumulate(vt[:500])
+    first = c.dump().cpu().numpy()
+    assert np.array_equal(first, oracle.to_int32(oracle.xmac(volt[:500])))
+    assert c.samples == 0
+    empty = c.dump().cpu().numpy()
+    assert not empty.any(), "an empty integration must dump zeros"
+    c.accumulate(vt[500:])
+    second = c.dump().cpu().numpy()
+    assert np.array_equal(second, oracle.to_int32(oracle.xmac(volt[500:])))
+    c.sync()
+    c.close()
+
+
+@pytest.mark.parametrize("path", ALL_PATHS)
+def test_host_buffers_exact(path):
+    N, F, T = 64, 5, 1234
+    if not path_available(path, N):
+        pytest.skip(f"{path} unsupported")
+    rng = np.random.default_rng(8)
+    volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    want = oracle.to_int32(oracle.xmac(volt))
+    assert np.array_equal(correlate(volt, path, host=True), want)
+    assert np.array_equal(correlate(volt, path, host=True, chunks=[(0, 1), (1, 1234)]), want)
+
+
+def test_overflow_and_state_errors():
+    c = corr.Correlator(16, 2, 100, path="cudacore")
+    v = torch.zeros((60, 2, 16), dtype=torch.uint8, device="cuda")
+    c.accumulate(v)
+    with pytest.raises(corr.CorrError) as e:
+        c.accumulate(v)
+    assert e.value.status == corr.CORR_E_OVERFLOW
+    assert c.samples == 60
+    with pytest.raises(corr.CorrError) as e:
+        c.set_path("mma_i8")
+    assert e.value.status == corr.CORR_E_STATE
+    with pytest.raises(ValueError):
+        c.accumulate(torch.zeros((4, 3, 16), dtype=torch.uint8, device="cuda"))
+    c.dump()
+    c.set_path("mma_i8")
+    c.sync()
+    c.close()
+
+
+@pytest.mark.parametrize("path", ALL_PATHS)
+def test_checkpoint_resume(path):
+    N, F, T = 64, 3, 800
+    if not path_available(path, N):
+        pytest.skip(f"{path} unsupported")
+    rng = np.random.default_rng(9)
+    volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    vt = torch.from_numpy(volt).cuda()
+    a = corr.Correlator(N, F, T, path=path)
+    a.accumulate(vt[:333])
+    state = a.get_state()
+    a.close()
+    b = corr.Correlator(N, F, T, path=path)
+    b.set_state(state)
+    assert b.samples == 333
+    b.accumulate(vt[333:])
+    got = b.dump().cpu().numpy()
+    b.close()
+    assert np.array_equal(got, oracle.to_int32(oracle.xmac(volt)))
+    bad = bytearray(state)
+    bad[8] ^= 1                                          # wrong N in the header
+    c = corr.Correlator(N, F, T, path=path)
+    with pytest.raises(corr.CorrError):
+        c.set_state(bytes(bad))
+    c.close()
+
+
+def test_unpack_matches_oracle_decode():
+    rng = np.random.default_rng(10)
+    volt = rng.integers(0, 256, (77, 3, 37), dtype=np.uint8)
+    volt[0, 0, :] = np.arange(37, dtype=np.uint8) * 7
+    for zi in (False, True):
+        re, im = oracle.decode(volt, zero_invalid=zi)
+        got = corr.unpack(torch.from_numpy(volt).cuda(), zero_invalid=zi).cpu().numpy()
+        want = np.stack([re, im], axis=-1).transpose(1, 2, 0, 3)   # [F][N][T][2]
+        assert np.array_equal(got.astype(np.int32), want)
+
+
+def test_paths_agree_with_each_other(coarse_volt):
+    volt, want = coarse_volt
+    sub = volt[:1500, :16]
+    outs = {p: correlate(sub, p) for p in _paths_for(256)}
+    ref = oracle.to_int32(oracle.xmac(sub))
+    for p, o in outs.items():
+        assert np.array_equal(o, ref), p
