@@ -184,6 +184,41 @@ int corr_set_state(corr_ctx *ctx, const void *h_buf, size_t bytes, void *stream)
 int corr_unpack(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs,
                 int8_t *d_out, unsigned flags, void *stream);
 
+/* ------------------------------------------------------- no device allocation -- */
+
+/* Size of the library's static device scratch used by corr_xmac_noalloc. */
+#define CORR_NOALLOC_SCRATCH_BYTES (64u << 20)
+
+/*
+ * One whole integration of one block, for callers that may not allocate
+ * device memory (no cudaMalloc, cudaFree or allocating library call happens
+ * here or in anything it calls).  This has no counterpart in the paper: it
+ * exists for hosts that own every byte of device memory through their own
+ * pool, and for real-time loops in which an allocation (and the device
+ * synchronisation it can cause) is not allowed once data is flowing.
+ *
+ * Correlates d_volt (device uint8 [n_time][n_chan][n_inputs], layout above)
+ * with the CUDA-core X-engine and OVERWRITES d_vis (device int32
+ * [n_chan][P][2]) with the packed triangle; n_time == 0 writes zeros.  Its
+ * scratch is one static device array of CORR_NOALLOC_SCRATCH_BYTES (64 MiB)
+ * that every GPU using the library holds until the process exits.  A request
+ * whose unpacked operands need more than that, i.e.
+ *     8 * n_chan * round_up(n_inputs, 64) * round_up(n_time, 64) / 2 bytes
+ * > CORR_NOALLOC_SCRATCH_BYTES, returns CORR_E_BUDGET without enqueuing
+ * anything (e.g. 256 inputs x 5000 samples fit 12 channels per call).
+ * Other argument errors: CORR_E_ARG.  Asynchronous on `stream`.
+ *
+ * The first call on each device looks up the scratch array's device address
+ * (cudaGetSymbolAddress, with that device current) and caches it; make that
+ * first call before any stream capture.  All calls on a device share the same
+ * scratch: calls whose work overlaps on the GPU (different streams, no
+ * ordering between them) race and corrupt each other's results.  Calls
+ * ordered on one stream are safe; the scratch keeps the previous call's
+ * contents, which the next call fully rewrites before reading.
+ */
+int corr_xmac_noalloc(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs,
+                      int32_t *d_vis, unsigned flags, void *stream);
+
 /* --------------------------------------------------------------- profiling -- */
 
 /* Kernel kinds counted by the profiler. */

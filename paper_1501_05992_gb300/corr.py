@@ -95,6 +95,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_get_state": ([vp, vp, c_size, vp], c_int),
             "corr_set_state": ([vp, vp, c_size, vp], c_int),
             "corr_unpack": ([vp, c_int, c_int, c_int, vp, ctypes.c_uint, vp], c_int),
+            "corr_xmac_noalloc": ([vp, c_int, c_int, c_int, vp, ctypes.c_uint, vp], c_int),
             "corr_profile_enable": ([vp, c_int], c_int),
             "corr_profile_read": ([vp, ctypes.POINTER(Profile), c_int], c_int),
             "corr_last_error": ([], c_int),

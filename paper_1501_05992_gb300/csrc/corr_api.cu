@@ -211,6 +211,8 @@ int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
 
 namespace corr {
 
+int set_last_error(int status) { return ret(status); }
+
 StagePlan plan_dp4a(int n_inputs, int n_chan, int t_max)
 {
     StagePlan P{};

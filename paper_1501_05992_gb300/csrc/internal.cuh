@@ -78,6 +78,9 @@ bool tc_supported(int n_inputs, int device);
 cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool zero_invalid,
                            int32_t *acc, bool fresh, DeviceStatus *status, cudaStream_t s);
 
+// Record `status` as the calling thread's last error and return it.
+int set_last_error(int status);
+
 // Dump: vis = acc (or zeros if `fresh`), n_words int32 words.  *launches
 // receives the number of kernels enqueued.
 cudaError_t launch_dump(const int32_t *acc, int32_t *vis, size_t n_words, bool fresh,
