@@ -152,10 +152,15 @@ int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
     cudaError_t e = cudaSuccess;
     const size_t row = size_t(c->f) * size_t(c->n);
     if (path == CORR_PATH_TC_FP8) {
-        prof_begin(c, s);
-        e = launch_xeng_tc(volt, c->f, c->n, nt, zi, c->acc, fresh, c->status, s);
-        prof_end(c, CORR_K_XENGINE, s, 1);
-        if (e != cudaSuccess) return cuda_fail(e);
+        for (int t0 = 0; t0 < nt; t0 += kTcMaxSamples) {
+            const int ntc = nt - t0 < kTcMaxSamples ? nt - t0 : kTcMaxSamples;
+            prof_begin(c, s);
+            e = launch_xeng_tc(volt + size_t(t0) * row, c->f, c->n, ntc, zi, c->acc, fresh,
+                               c->status, s);
+            prof_end(c, CORR_K_XENGINE, s, 1);
+            if (e != cudaSuccess) return cuda_fail(e);
+            fresh = false;
+        }
     } else if (path == CORR_PATH_CUDACORE) {
         const StagePlan &P = c->dp4a;
         const size_t plane_max = size_t(P.f_chunk) * (P.t_chunk / 2) * P.n_pad;

@@ -17,6 +17,7 @@ constexpr int kMmaTile = 64;           // int8 mma.sync tile (inputs per side)
 constexpr int kMmaKT = 64;             // samples per K stage of the mma.sync kernel
 constexpr size_t kStageCap = size_t(1) << 30;  // unpacked-operand staging cap, bytes
 constexpr int kHostChunk = 500;        // samples per host->device transfer chunk
+constexpr int kTcMaxSamples = 32768;   // tcgen05 path: samples per launch (FP32 sums < 2^24)
 constexpr size_t kAlign = 256;
 
 __host__ __device__ inline long long n_pairs(long long n) { return n * (n + 1) / 2; }
@@ -73,7 +74,6 @@ cudaError_t launch_xeng_mma8(const int8_t *X, const int8_t *Xt, int n, int n_pad
                              int t_pad, int32_t *acc, int f0, bool fresh, cudaStream_t s);
 
 // tcgen05 FP8 X-engine straight from packed voltages (no staging).
-struct TcPlan;
 bool tc_supported(int n_inputs, int device);
 cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool zero_invalid,
                            int32_t *acc, bool fresh, DeviceStatus *status, cudaStream_t s);

@@ -1,15 +1,666 @@
-// X-engine, tcgen05 FP8 form (K2c).  Placeholder until the tensor-core
-// kernel lands: reports the path as unsupported.
+// X-engine, tcgen05 FP8 tensor-core form (K2c), fused with the unpack.
+//
+// What it computes is Eq. 3 (Section 2) integrated over time (Section 3.4.2):
+// V_ij(f) = sum_t x_i(t,f) conj(x_j(t,f)) for j <= i, straight from the
+// packed 4+4-bit voltages volt[t][f][n] (Appendix A, Appendix C "GPU Input"),
+// into the packed lower triangle of Appendix C "GPU Output".  The paper's GPU
+// kernel (xGPU) tiles baselines per thread block and integrates in registers
+// (Section 3.4.2, Eq. 4); here a baseline tile is a 128 x 128 block of inputs
+// integrated in tensor memory (TMEM) by tcgen05.mma.
+//
+// Encoding (exact): each 4-bit two's-complement component v in [-8, 7] is
+// coded as u = v + 8 in [0, 15], and the E4M3 byte with bit pattern u
+// (0x00..0x0F) has the value u * 2^-9: codes 1..7 are subnormals, 8..15 the
+// first normal binade, so the byte map is one XOR with 0x08 per nibble.  The
+// tensor core then computes, per sample, products u_i u_j * 2^-18, exact in
+// FP32, and FP32 accumulation stays exact while |sum| < 2^24 (measured on
+// sm_103a; the host splits calls at kTcMaxSamples so the bound always holds).
+// With ur, um the codes of the real and imaginary parts:
+//
+//   P_re = sum(ur_i ur_j + um_i um_j),  P_im = sum(um_i ur_j - ur_i um_j)
+//   Re V_ij = P_re - 8 (E_i + E_j) + 128 T,   Im V_ij = P_im - 8 D_i + 8 D_j
+//
+// with E_k = sum(ur_k + um_k), D_k = sum(um_k - ur_k) over the T processed
+// samples (samples past the end of the block are zero bytes, i.e. u = 8, and
+// cancel exactly).
+//
+// Complex -> real: with planes R (ur), M (um), nM (-um) of the J tile, two
+// MMAs per 32 samples, each M=128 x N=256 x K=32, fill D = [Re | Im]:
+//   D += R_I . [R_J ; nM_J]^T   ->  [ sum ur ur | -sum ur um ]
+//   D += M_I . [M_J ; R_J ]^T   ->  [ sum um um |  sum um ur ]
+// Operands are MN-major (inputs contiguous, the natural [t][n] order of the
+// voltages), 128-byte swizzled, so no transpose is ever needed.
+//
+// Pipeline (persistent, one CTA per SM, work item = (channel, I tile, J tile)):
+//   warp 0     TMA producer: packed bytes [64 samples][128 inputs] per tile
+//   warp 1     TMEM allocator and single-thread MMA issuer
+//   warps 2-9  converters: packed bytes -> E4M3 planes (+ per-input sums)
+//   warps 10-13 epilogue: TMEM -> int32, corrections, packed-triangle store
+// Accumulators are double-buffered in TMEM (2 x 256 columns) so the epilogue
+// of one item overlaps the main loop of the next.  Every wait is bounded: on
+// a timeout the kernel records CORR_E_TIMEOUT, drains its own copies and MMAs,
+// frees TMEM and returns.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
 #include "internal.cuh"
 
 namespace corr {
+namespace {
 
-bool tc_supported(int, int) { return false; }
+constexpr int kTile = 128;                    // inputs per tile side
+constexpr int kTc = 64;                       // samples per pipeline stage
+constexpr int kPackedStages = 4;
+constexpr int kPlaneStages = 3;
+constexpr int kPlaneBytes = kTc * 128;        // one E4M3 plane: 64 rows x 128 B = 8 KB
+constexpr int kPackedTileBytes = kTc * kTile; // 8 KB
+constexpr int kPackedStageBytes = 2 * kPackedTileBytes;
+// plane stage layout: R_I | M_I | M_J | R_J | nM_J
+constexpr int kOffRI = 0, kOffMI = kPlaneBytes, kOffMJ = 2 * kPlaneBytes, kOffRJ = 3 * kPlaneBytes,
+              kOffNMJ = 4 * kPlaneBytes;
+constexpr int kPlaneStageBytes = 5 * kPlaneBytes;  // 40 KB
+constexpr int kConvWarps = 8, kEpiWarps = 4;
+constexpr int kThreads = (2 + kConvWarps + kEpiWarps) * 32;   // 448
+constexpr int kFirstConvWarp = 2, kFirstEpiWarp = 2 + kConvWarps;
+constexpr int kTmemCols = 512;               // 2 accumulator buffers x (128 Re + 128 Im)
+constexpr long long kWaitLimit = 1LL << 31;  // clock64 cycles (about 1 s)
 
-cudaError_t launch_xeng_tc(const uint8_t *, int, int, int, bool, int32_t *, bool,
-                           DeviceStatus *, cudaStream_t)
+// shared-memory map (offsets from a 1024-aligned base)
+constexpr int kSmPacked = 0;
+constexpr int kSmPlanes = kSmPacked + kPackedStages * kPackedStageBytes;          // 64 KB
+constexpr int kSmSums = kSmPlanes + kPlaneStages * kPlaneStageBytes;              // +120 KB
+constexpr int kSumsBytes = 2 * 2 * kTile * 2 * 4;                                 // [buf][tile][n][r/m]
+constexpr int kSmBars = kSmSums + kSumsBytes;
+constexpr int kNumBars = 2 * kPackedStages + 2 * kPlaneStages + 4 + 4 + 1;
+constexpr int kSmMisc = kSmBars + kNumBars * 8;
+constexpr int kSmemBytes = kSmMisc + 64 + 1024;                                   // + alignment slack
+
+// instruction descriptor: kind::f8f6f4, E4M3 x E4M3 -> F32, both MN-major, M=128, N=256
+constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | (1u << 15) | (1u << 16) |
+                            ((256u >> 3) << 17) | ((128u >> 4) << 24);
+
+struct Params {
+    int n, n_chan, nt, n_tiles, n_items, n_stages;
+    int zero_invalid, fresh;
+    int32_t *acc;
+    DeviceStatus *status;
+};
+
+// ------------------------------------------------------------ PTX helpers --
+__device__ __forceinline__ uint32_t smem_u32(const void *p)
 {
-    return cudaErrorNotSupported;
+    return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count)
+{
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar)
+{
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes)
+{
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity)
+        : "memory");
+    return done != 0;
+}
+
+// Bounded wait.  Returns false on timeout or if another role aborted.
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort,
+                                          DeviceStatus *status, int where)
+{
+    if (mbar_try(bar, parity)) return true;
+    const long long t0 = clock64();
+    while (true) {
+        if (mbar_try(bar, parity)) return true;
+        if (*abort) return false;
+        if (clock64() - t0 > kWaitLimit) {
+            *abort = 1;
+            if (atomicCAS(&status->code, 0, CORR_E_TIMEOUT) == 0) {
+                status->where = where;
+                status->detail0 = int(blockIdx.x);
+            }
+            return false;
+        }
+    }
+}
+
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
+                                            int x, int y, int z)
+{
+    asm volatile(
+        "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+        " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+        "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+        : "memory");
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
+{
+    uint64_t d = 0;
+    d |= uint64_t((saddr >> 4) & 0x3FFFu);
+    d |= uint64_t((lbo >> 4) & 0x3FFFu) << 16;
+    d |= uint64_t((sbo >> 4) & 0x3FFFu) << 32;
+    d |= uint64_t(1) << 46;                     // descriptor version
+    d |= uint64_t(2) << 61;                     // 128-byte swizzle
+    return d;
+}
+
+__device__ __forceinline__ void mma_f8(uint32_t tmem, uint64_t a, uint64_t b, uint32_t accum)
+{
+    asm volatile(
+        "{\n .reg .pred p;\n setp.ne.b32 p, %4, 0;\n"
+        " tcgen05.mma.cta_group::1.kind::f8f6f4 [%0], %1, %2, %3, p;\n}\n" ::"r"(tmem),
+        "l"(a), "l"(b), "r"(kIdesc), "r"(accum));
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar)
+{
+    asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+                 : "memory");
+}
+
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
+{
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+          "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+}
+
+__device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
+
+__device__ __forceinline__ void named_sync(int id, int threads)
+{
+    asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
+}
+
+__device__ __forceinline__ void item_tiles(int p, int &I, int &J)
+{
+    int i = int((sqrtf(8.0f * float(p) + 1.0f) - 1.0f) * 0.5f);
+    while ((i + 1) * (i + 2) / 2 <= p) ++i;
+    while (i * (i + 1) / 2 > p) --i;
+    I = i;
+    J = p - i * (i + 1) / 2;
+}
+
+// 4 packed bytes (r << 4 | m) -> E4M3 codes u = nibble ^ 8 (value u * 2^-9).
+__device__ __forceinline__ void codes(uint32_t w, bool zero_invalid, uint32_t &R, uint32_t &M)
+{
+    R = ((w >> 4) & 0x0F0F0F0Fu) ^ 0x08080808u;
+    M = (w & 0x0F0F0F0Fu) ^ 0x08080808u;
+    if (zero_invalid) {
+        // a nibble code of 8 (value -8) has u == 0: such samples become 0 + 0i (u = 8, 8)
+        const uint32_t nzR = (R + 0x7F7F7F7Fu) & 0x80808080u;   // bit 7 set where u != 0
+        const uint32_t nzM = (M + 0x7F7F7F7Fu) & 0x80808080u;
+        const uint32_t bad = (~(nzR & nzM)) & 0x80808080u;      // bit 7 set where invalid
+        const uint32_t mask = (bad >> 7) * 0xFFu;
+        R = (R & ~mask) | (0x08080808u & mask);
+        M = (M & ~mask) | (0x08080808u & mask);
+    }
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
+{
+    extern __shared__ uint8_t smem_raw[];
+    uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+    const uint32_t sbase = smem_u32(smem);
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+
+    int *sums = reinterpret_cast<int *>(smem + kSmSums);
+    const uint32_t bars = sbase + kSmBars;
+    auto bar_packed_full = [&](int s) { return bars + 8u * s; };
+    auto bar_packed_empty = [&](int s) { return bars + 8u * (kPackedStages + s); };
+    auto bar_plane_full = [&](int s) { return bars + 8u * (2 * kPackedStages + s); };
+    auto bar_plane_empty = [&](int s) { return bars + 8u * (2 * kPackedStages + kPlaneStages + s); };
+    auto bar_acc_full = [&](int b) { return bars + 8u * (2 * kPackedStages + 2 * kPlaneStages + b); };
+    auto bar_acc_empty = [&](int b) { return bars + 8u * (2 * kPackedStages + 2 * kPlaneStages + 2 + b); };
+    auto bar_sums_full = [&](int b) { return bars + 8u * (2 * kPackedStages + 2 * kPlaneStages + 4 + b); };
+    auto bar_sums_empty = [&](int b) { return bars + 8u * (2 * kPackedStages + 2 * kPlaneStages + 6 + b); };
+    const uint32_t bar_drain = bars + 8u * (2 * kPackedStages + 2 * kPlaneStages + 8);
+    uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kSmMisc);
+    volatile int *abort = reinterpret_cast<volatile int *>(smem + kSmMisc + 8);
+    volatile int *epi_ok = reinterpret_cast<volatile int *>(smem + kSmMisc + 16);
+
+    if (threadIdx.x == 0) {
+        for (int s = 0; s < kPackedStages; ++s) {
+            mbar_init(bar_packed_full(s), 1);
+            mbar_init(bar_packed_empty(s), kConvWarps);
+        }
+        for (int s = 0; s < kPlaneStages; ++s) {
+            mbar_init(bar_plane_full(s), kConvWarps);
+            mbar_init(bar_plane_empty(s), 1);
+        }
+        for (int b = 0; b < 2; ++b) {
+            mbar_init(bar_acc_full(b), 1);
+            mbar_init(bar_acc_empty(b), kEpiWarps);
+            mbar_init(bar_sums_full(b), kConvWarps);
+            mbar_init(bar_sums_empty(b), kEpiWarps);
+        }
+        mbar_init(bar_drain, 1);
+        *abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+    }
+    for (int e = threadIdx.x; e < kSumsBytes / 4; e += kThreads) sums[e] = 0;
+    if (warp == 1) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                     "r"(kTmemCols));
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+    }
+    fence_before();
+    __syncthreads();
+    fence_after();
+    const uint32_t tmem = *tmem_slot;
+    const int first_item = blockIdx.x, item_step = gridDim.x;
+
+    if (warp == 0) {
+        // ------------------------------------------------- TMA producer --
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            int issued[kPackedStages];            // parity of the last load issued into each slot, or -1
+            for (int k = 0; k < kPackedStages; ++k) issued[k] = -1;
+            bool ok = true;
+            for (int item = first_item; ok && item < p.n_items; item += item_step) {
+                const int f = item / ((p.n_tiles * (p.n_tiles + 1)) / 2);
+                int I, J;
+                item_tiles(item % ((p.n_tiles * (p.n_tiles + 1)) / 2), I, J);
+                const bool diag = I == J;
+                for (int s = 0; s < p.n_stages; ++s) {
+                    if (!mbar_wait(bar_packed_empty(stage), phase ^ 1u, abort, p.status, 1)) {
+                        ok = false;
+                        break;
+                    }
+                    const uint32_t full = bar_packed_full(stage);
+                    const uint32_t dst = sbase + kSmPacked + stage * kPackedStageBytes;
+                    mbar_expect_tx(full, diag ? kPackedTileBytes : 2 * kPackedTileBytes);
+                    tma_load_3d(dst + kPackedTileBytes, &tmap, full, J * kTile, f, s * kTc);
+                    if (!diag) tma_load_3d(dst, &tmap, full, I * kTile, f, s * kTc);
+                    issued[stage] = int(phase);
+                    if (++stage == kPackedStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+            }
+            // every issued load must have landed before the CTA may exit
+            for (int k = 0; k < kPackedStages; ++k) {
+                if (issued[k] < 0) continue;
+                const long long t0 = clock64();
+                while (!mbar_try(bar_packed_full(k), uint32_t(issued[k])) && clock64() - t0 < kWaitLimit) {
+                }
+            }
+        }
+    } else if (warp == 1) {
+        // ---------------------------------------------------- MMA issuer --
+        if (lane == 0) {
+            int stage = 0;
+            uint32_t phase = 0;
+            uint32_t acc_phase[2] = {0, 0};
+            int local = 0;
+            bool ok = true;
+            for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
+                int I, J;
+                item_tiles(item % ((p.n_tiles * (p.n_tiles + 1)) / 2), I, J);
+                const bool diag = I == J;
+                const int buf = local & 1;
+                if (!mbar_wait(bar_acc_empty(buf), acc_phase[buf] ^ 1u, abort, p.status, 2)) {
+                    ok = false;
+                    break;
+                }
+                acc_phase[buf] ^= 1u;
+                fence_after();
+                const uint32_t d_tmem = tmem + uint32_t(buf * 256);
+                uint32_t accum = 0;
+                for (int s = 0; s < p.n_stages; ++s) {
+                    if (!mbar_wait(bar_plane_full(stage), phase, abort, p.status, 3)) {
+                        ok = false;
+                        break;
+                    }
+                    fence_after();
+                    const uint32_t ps = sbase + kSmPlanes + stage * kPlaneStageBytes;
+                    const uint32_t aR = ps + (diag ? kOffRJ : kOffRI);
+                    const uint32_t aM = ps + (diag ? kOffMJ : kOffMI);
+#pragma unroll
+                    for (int ks = 0; ks < kTc / 32; ++ks) {
+                        const uint32_t ko = uint32_t(ks) * 4096u;
+                        mma_f8(d_tmem, smem_desc(aR + ko, kPlaneBytes, 1024),
+                               smem_desc(ps + kOffRJ + ko, kPlaneBytes, 1024), accum);
+                        accum = 1;
+                        mma_f8(d_tmem, smem_desc(aM + ko, kPlaneBytes, 1024),
+                               smem_desc(ps + kOffMJ + ko, kPlaneBytes, 1024), 1);
+                    }
+                    mma_commit(bar_plane_empty(stage));
+                    if (++stage == kPlaneStages) {
+                        stage = 0;
+                        phase ^= 1u;
+                    }
+                }
+                if (!ok) break;
+                mma_commit(bar_acc_full(buf));
+            }
+            // drain all MMAs issued by this thread before TMEM is released
+            mma_commit(bar_drain);
+            const long long t0 = clock64();
+            while (!mbar_try(bar_drain, 0) && clock64() - t0 < kWaitLimit) {
+            }
+        }
+    } else if (warp < kFirstEpiWarp) {
+        // ----------------------------------------------------- converters --
+        const int ct = threadIdx.x - kFirstConvWarp * 32;        // 0..255
+        const int c = ct & 7, r0 = ct >> 3;                       // chunk column, first row
+        const bool zi = p.zero_invalid != 0;
+        int pstage = 0, cstage = 0;
+        uint32_t pphase = 0, cphase = 0;
+        uint32_t sphase[2] = {0, 0};
+        int local = 0;
+        bool ok = true;
+        for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
+            int I, J;
+            item_tiles(item % ((p.n_tiles * (p.n_tiles + 1)) / 2), I, J);
+            const bool diag = I == J;
+            // per-input code sums of this thread's 16 inputs (4 words x 4 bytes):
+            // byte lanes (<= 16 rows) then 16-bit lanes
+            uint32_t b8[2][2][4], s16lo[2][2][4], s16hi[2][2][4];
+#pragma unroll
+            for (int t = 0; t < 2; ++t)
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) b8[t][q][k] = s16lo[t][q][k] = s16hi[t][q][k] = 0;
+            for (int s = 0; s < p.n_stages; ++s) {
+                if (!mbar_wait(bar_packed_full(pstage), pphase, abort, p.status, 4) ||
+                    !mbar_wait(bar_plane_empty(cstage), cphase ^ 1u, abort, p.status, 5)) {
+                    ok = false;
+                    break;
+                }
+                const uint8_t *pk = smem + kSmPacked + pstage * kPackedStageBytes;
+                uint8_t *pl = smem + kSmPlanes + cstage * kPlaneStageBytes;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int row = r0 + 32 * h;
+                    const uint32_t so = uint32_t(row * 128 + ((c ^ (row & 7)) << 4));
+                    // J tile: planes M, R, nM
+                    {
+                        const uint4 w = *reinterpret_cast<const uint4 *>(pk + kPackedTileBytes + row * 128 + c * 16);
+                        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+                        uint32_t R[4], M[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            codes(ww[k], zi, R[k], M[k]);
+                            b8[1][0][k] += R[k];
+                            b8[1][1][k] += M[k];
+                        }
+                        *reinterpret_cast<uint4 *>(pl + kOffMJ + so) = make_uint4(M[0], M[1], M[2], M[3]);
+                        *reinterpret_cast<uint4 *>(pl + kOffRJ + so) = make_uint4(R[0], R[1], R[2], R[3]);
+                        *reinterpret_cast<uint4 *>(pl + kOffNMJ + so) =
+                            make_uint4(M[0] | 0x80808080u, M[1] | 0x80808080u, M[2] | 0x80808080u,
+                                       M[3] | 0x80808080u);
+                    }
+                    if (!diag) {
+                        const uint4 w = *reinterpret_cast<const uint4 *>(pk + row * 128 + c * 16);
+                        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
+                        uint32_t R[4], M[4];
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            codes(ww[k], zi, R[k], M[k]);
+                            b8[0][0][k] += R[k];
+                            b8[0][1][k] += M[k];
+                        }
+                        *reinterpret_cast<uint4 *>(pl + kOffRI + so) = make_uint4(R[0], R[1], R[2], R[3]);
+                        *reinterpret_cast<uint4 *>(pl + kOffMI + so) = make_uint4(M[0], M[1], M[2], M[3]);
+                    }
+                }
+                asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+                __syncwarp();
+                if (lane == 0) {
+                    mbar_arrive(bar_plane_full(cstage));
+                    mbar_arrive(bar_packed_empty(pstage));
+                }
+                if (++pstage == kPackedStages) {
+                    pstage = 0;
+                    pphase ^= 1u;
+                }
+                if (++cstage == kPlaneStages) {
+                    cstage = 0;
+                    cphase ^= 1u;
+                }
+                // byte lanes hold at most 16 rows of codes <= 15 (255): widen every 8 stages
+                if ((s & 7) == 7 || s + 1 == p.n_stages) {
+#pragma unroll
+                    for (int t = 0; t < 2; ++t)
+#pragma unroll
+                        for (int q = 0; q < 2; ++q)
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                s16lo[t][q][k] += b8[t][q][k] & 0x00FF00FFu;
+                                s16hi[t][q][k] += (b8[t][q][k] >> 8) & 0x00FF00FFu;
+                                b8[t][q][k] = 0;
+                            }
+                }
+            }
+            if (!ok) break;
+            // hand the per-input sums of this item to the epilogue
+            const int buf = local & 1;
+            if (!mbar_wait(bar_sums_empty(buf), sphase[buf] ^ 1u, abort, p.status, 6)) {
+                ok = false;
+                break;
+            }
+            sphase[buf] ^= 1u;
+            int *sb = sums + buf * (2 * kTile * 2);
+#pragma unroll
+            for (int t = 0; t < 2; ++t) {
+                if (t == 0 && diag) continue;
+#pragma unroll
+                for (int q = 0; q < 2; ++q)
+#pragma unroll
+                    for (int k = 0; k < 4; ++k) {
+                        const int n0 = c * 16 + 4 * k;
+                        int *dst = sb + (t * kTile + n0) * 2 + q;
+                        atomicAdd(dst + 0, int(s16lo[t][q][k] & 0xFFFFu));
+                        atomicAdd(dst + 2, int(s16hi[t][q][k] & 0xFFFFu));
+                        atomicAdd(dst + 4, int(s16lo[t][q][k] >> 16));
+                        atomicAdd(dst + 6, int(s16hi[t][q][k] >> 16));
+                    }
+            }
+            __syncwarp();
+            if (lane == 0) mbar_arrive(bar_sums_full(buf));
+        }
+    } else {
+        // ------------------------------------------------------- epilogue --
+        const int q = warp & 3;                      // TMEM lane quarter of this warp
+        uint32_t aphase[2] = {0, 0};
+        int local = 0;
+        bool ok = true;
+        const long long P = n_pairs(p.n);
+        const int T_eff = p.n_stages * kTc;
+        for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
+            const int f = item / ((p.n_tiles * (p.n_tiles + 1)) / 2);
+            int I, J;
+            item_tiles(item % ((p.n_tiles * (p.n_tiles + 1)) / 2), I, J);
+            const bool diag = I == J;
+            const int buf = local & 1;
+            // the four epilogue warps decide together whether to go on, so that
+            // none of them is ever left waiting at a named barrier
+            const bool mine = mbar_wait(bar_acc_full(buf), aphase[buf], abort, p.status, 7) &&
+                              mbar_wait(bar_sums_full(buf), aphase[buf], abort, p.status, 8);
+            if (lane == 0) epi_ok[q] = mine ? 1 : 0;
+            named_sync(2, kEpiWarps * 32);
+            ok = epi_ok[0] && epi_ok[1] && epi_ok[2] && epi_ok[3];
+            named_sync(2, kEpiWarps * 32);
+            if (!ok) break;
+            aphase[buf] ^= 1u;
+            fence_after();
+            int *sb = sums + buf * (2 * kTile * 2);
+            const int *si = sb + (diag ? kTile : 0) * 2;      // I tile sums
+            const int *sj = sb + kTile * 2;                    // J tile sums
+            const int il = q * 32 + lane;
+            const int i = I * kTile + il;
+            const int Ei = si[il * 2] + si[il * 2 + 1];
+            const int Di = si[il * 2 + 1] - si[il * 2];
+            const int base_re = 128 * T_eff - 8 * Ei;
+            int32_t *out = p.acc + ((size_t)f * P + (size_t)i * (i + 1) / 2) * 2;
+            const uint32_t taddr = tmem + uint32_t(buf * 256) + (uint32_t(q * 32) << 16);
+#pragma unroll 1
+            for (int c0 = 0; c0 < kTile; c0 += 16) {
+                uint32_t vre[16], vim[16];
+                tmem_ld16(taddr + c0, vre);
+                tmem_ld16(taddr + 128 + c0, vim);
+                tmem_wait_ld();
+                if (i < p.n) {
+#pragma unroll
+                    for (int k = 0; k < 16; ++k) {
+                        const int jl = c0 + k;
+                        const int j = J * kTile + jl;
+                        if (j > i) break;
+                        const int Ej = sj[jl * 2] + sj[jl * 2 + 1];
+                        const int Dj = sj[jl * 2 + 1] - sj[jl * 2];
+                        const int pre = __float2int_rn(__uint_as_float(vre[k]) * 262144.0f);
+                        const int pim = __float2int_rn(__uint_as_float(vim[k]) * 262144.0f);
+                        const int re = pre + base_re - 8 * Ej;
+                        const int im = pim - 8 * Di + 8 * Dj;
+                        int2 *dst = reinterpret_cast<int2 *>(out + size_t(j) * 2);
+                        if (p.fresh) {
+                            *dst = make_int2(re, im);
+                        } else {
+                            int2 v = *dst;
+                            v.x += re;
+                            v.y += im;
+                            *dst = v;
+                        }
+                    }
+                }
+            }
+            fence_before();
+            // every epilogue warp has read this item's sums: clear them for the
+            // item that reuses the buffer, then release TMEM and sums
+            named_sync(2, kEpiWarps * 32);
+            for (int e = threadIdx.x - kFirstEpiWarp * 32; e < 2 * kTile * 2; e += kEpiWarps * 32) sb[e] = 0;
+            __syncwarp();
+            if (lane == 0) {
+                mbar_arrive(bar_acc_empty(buf));
+                mbar_arrive(bar_sums_empty(buf));
+            }
+        }
+    }
+
+    fence_before();
+    __syncthreads();
+    fence_after();
+    if (warp == 1) {
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+    }
+}
+
+// ------------------------------------------------------------- host side --
+PFN_cuTensorMapEncodeTiled_v12000 g_encode = nullptr;
+std::once_flag g_encode_once;
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder()
+{
+    std::call_once(g_encode_once, [] {
+        void *fn = nullptr;
+        cudaDriverEntryPointQueryResult q;
+        if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) ==
+                cudaSuccess &&
+            q == cudaDriverEntryPointSuccess)
+            g_encode = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(fn);
+        else
+            cudaGetLastError();
+    });
+    return g_encode;
+}
+
+int g_sm_count[64] = {0};
+int g_attr_set[64] = {0};
+std::mutex g_dev_mu;
+
+}  // namespace
+
+bool tc_supported(int n_inputs, int device)
+{
+    if (n_inputs % 16 != 0 || device < 0 || device >= 64) return false;
+    static int cached[64] = {0};                 // 0 unknown, 1 yes, -1 no
+    if (cached[device] == 0) {
+        cudaDeviceProp prop;
+        bool ok = cudaGetDeviceProperties(&prop, device) == cudaSuccess && prop.major == 10 &&
+                  prop.minor == 3 && prop.sharedMemPerBlockOptin >= size_t(kSmemBytes) &&
+                  encoder() != nullptr;
+        cudaGetLastError();
+        cached[device] = ok ? 1 : -1;
+    }
+    return cached[device] == 1;
+}
+
+cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool zero_invalid,
+                           int32_t *acc, bool fresh, DeviceStatus *status, cudaStream_t s)
+{
+    if (nt <= 0) return cudaSuccess;
+    if (nt > kTcMaxSamples || n % 16 != 0 || (reinterpret_cast<uintptr_t>(volt) & 15) != 0)
+        return cudaErrorInvalidValue;
+    auto enc = encoder();
+    if (!enc) return cudaErrorNotSupported;
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+    {
+        std::lock_guard<std::mutex> lock(g_dev_mu);
+        if (!g_attr_set[dev]) {
+            e = cudaFuncSetAttribute(xeng_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+            if (e != cudaSuccess) return e;
+            e = cudaDeviceGetAttribute(&g_sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
+            if (e != cudaSuccess) return e;
+            g_attr_set[dev] = 1;
+        }
+    }
+    CUtensorMap map;
+    const cuuint64_t dims[3] = {cuuint64_t(n), cuuint64_t(n_chan), cuuint64_t(nt)};
+    const cuuint64_t strides[2] = {cuuint64_t(n), cuuint64_t(n) * cuuint64_t(n_chan)};
+    const cuuint32_t box[3] = {cuuint32_t(kTile), 1u, cuuint32_t(kTc)};
+    const cuuint32_t estr[3] = {1u, 1u, 1u};
+    CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(volt), dims, strides, box,
+                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    Params prm{};
+    prm.n = n;
+    prm.n_chan = n_chan;
+    prm.nt = nt;
+    prm.n_tiles = (n + kTile - 1) / kTile;
+    prm.n_items = n_chan * (prm.n_tiles * (prm.n_tiles + 1) / 2);
+    prm.n_stages = (nt + kTc - 1) / kTc;
+    prm.zero_invalid = zero_invalid ? 1 : 0;
+    prm.fresh = fresh ? 1 : 0;
+    prm.acc = acc;
+    prm.status = status;
+    const int grid = prm.n_items < g_sm_count[dev] ? prm.n_items : g_sm_count[dev];
+    xeng_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(map, prm);
+    return cudaGetLastError();
 }
 
 }  // namespace corr

@@ -196,3 +196,32 @@ def test_paths_agree_with_each_other(coarse_volt):
     ref = oracle.to_int32(oracle.xmac(sub))
     for p, o in outs.items():
         assert np.array_equal(o, ref), p
+
+
+@pytest.mark.parametrize("path", ALL_PATHS)
+def test_long_integration_worst_case_magnitude(path):
+    """All samples 7+7i for 40000 samples: the largest sums the tensor-core
+    encoding produces (its FP32 partials peak at 450 x 32768 < 2^24 per launch),
+    across the split into several launches."""
+    N, F, T = 128, 2, 40000
+    if not path_available(path, N):
+        pytest.skip(f"{path} unsupported")
+    volt = np.full((T, F, N), 0x77, np.uint8)
+    volt[:, 1, ::3] = 0x88                        # -8-8i on every third input of channel 1
+    volt[::7, 1, 1::3] = 0x79
+    want = oracle.to_int32(oracle.xmac(volt))
+    assert np.array_equal(correlate(volt, path), want)
+    got = correlate(volt, path, chunks=[(0, 32767), (32767, 32769), (32769, T)])
+    assert np.array_equal(got, want)
+
+
+@pytest.mark.parametrize("path", ALL_PATHS)
+def test_many_channels_and_tiles(path):
+    """More work items than SMs: 384 inputs (6 tile pairs per channel) x 40 ch."""
+    N, F, T = 384, 40, 200
+    if not path_available(path, N):
+        pytest.skip(f"{path} unsupported")
+    rng = np.random.default_rng(12)
+    volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    want = oracle.to_int32(oracle.xmac(volt))
+    assert np.array_equal(correlate(volt, path), want)
