@@ -32,10 +32,11 @@
 // voltages), 128-byte swizzled, so no transpose is ever needed.
 //
 // Pipeline (persistent, one CTA per SM, work item = (channel, I tile, J tile)):
-//   warp 0     TMA producer: packed bytes [64 samples][128 inputs] per tile
+//   warp 0     TMA producer: packed bytes [64 samples][128 inputs] per tile,
+//              with L2 prefetch of the tiles kPrefetchStages stages ahead
 //   warp 1     TMEM allocator and single-thread MMA issuer
-//   warps 2-9  converters: packed bytes -> E4M3 planes (+ per-input sums)
-//   warps 10-13 epilogue: TMEM -> int32, corrections, packed-triangle store
+//   warps 2-17 converters: packed bytes -> E4M3 planes (+ per-input sums)
+//   warps 18-21 epilogue: TMEM -> int32, corrections, packed-triangle store
 // Accumulators are double-buffered in TMEM (2 x 256 columns) so the epilogue
 // of one item overlaps the main loop of the next.  Every wait is bounded: on
 // a timeout the kernel records CORR_E_TIMEOUT, drains its own copies and MMAs,
@@ -52,7 +53,8 @@ namespace {
 
 constexpr int kTile = 128;                    // inputs per tile side
 constexpr int kTc = 64;                       // samples per pipeline stage
-constexpr int kPackedStages = 4;
+constexpr int kPackedStages = 6;
+constexpr int kPrefetchStages = 12;           // L2 prefetch distance of the packed loads
 constexpr int kPlaneStages = 3;
 constexpr int kPlaneBytes = kTc * 128;        // one E4M3 plane: 64 rows x 128 B = 8 KB
 constexpr int kPackedTileBytes = kTc * kTile; // 8 KB
@@ -61,8 +63,8 @@ constexpr int kPackedStageBytes = 2 * kPackedTileBytes;
 constexpr int kOffRI = 0, kOffMI = kPlaneBytes, kOffMJ = 2 * kPlaneBytes, kOffRJ = 3 * kPlaneBytes,
               kOffNMJ = 4 * kPlaneBytes;
 constexpr int kPlaneStageBytes = 5 * kPlaneBytes;  // 40 KB
-constexpr int kConvWarps = 8, kEpiWarps = 4;
-constexpr int kThreads = (2 + kConvWarps + kEpiWarps) * 32;   // 448
+constexpr int kConvWarps = 16, kEpiWarps = 4;
+constexpr int kThreads = (2 + kConvWarps + kEpiWarps) * 32;   // 704
 constexpr int kFirstConvWarp = 2, kFirstEpiWarp = 2 + kConvWarps;
 constexpr int kTmemCols = 512;               // 2 accumulator buffers x (128 Re + 128 Im)
 constexpr long long kWaitLimit = 1LL << 31;  // clock64 cycles (about 1 s)
@@ -71,7 +73,7 @@ constexpr long long kWaitLimit = 1LL << 31;  // clock64 cycles (about 1 s)
 constexpr int kSmPacked = 0;
 constexpr int kSmPlanes = kSmPacked + kPackedStages * kPackedStageBytes;          // 64 KB
 constexpr int kSmSums = kSmPlanes + kPlaneStages * kPlaneStageBytes;              // +120 KB
-constexpr int kSumsBytes = 2 * 2 * kTile * 2 * 4;                                 // [buf][tile][n][r/m]
+constexpr int kSumsBytes = 2 * 2 * 2 * kTile * 4;                                 // [buf][tile][r/m][slot]
 constexpr int kSmBars = kSmSums + kSumsBytes;
 constexpr int kNumBars = 2 * kPackedStages + 2 * kPlaneStages + 4 + 4 + 1;
 constexpr int kSmMisc = kSmBars + kNumBars * 8;
@@ -142,6 +144,46 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     }
 }
 
+// Warp-wide bounded wait: lane 0 polls (with an optional back-off), then every
+// lane confirms once, so each lane gets the barrier's acquire ordering while
+// only one lane keeps hitting shared memory.
+__device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort,
+                                          DeviceStatus *status, int where, int lane,
+                                          unsigned sleep_ns = 0)
+{
+    int ok = 1;
+    if (lane == 0) {
+        if (!mbar_try(bar, parity)) {
+            const long long t0 = clock64();
+            while (true) {
+                if (mbar_try(bar, parity)) break;
+                if (*abort) {
+                    ok = 0;
+                    break;
+                }
+                if (clock64() - t0 > kWaitLimit) {
+                    *abort = 1;
+                    if (atomicCAS(&status->code, 0, CORR_E_TIMEOUT) == 0) {
+                        status->where = where;
+                        status->detail0 = int(blockIdx.x);
+                    }
+                    ok = 0;
+                    break;
+                }
+                if (sleep_ns) __nanosleep(sleep_ns);
+            }
+        }
+    }
+    ok = __shfl_sync(0xFFFFFFFFu, ok, 0);
+    if (!ok) return false;
+    return mbar_try(bar, parity);        // completed: returns at once, with acquire
+}
+
+// index of input n (0..127) in a row of per-input sums: [n % 16][n / 16], so
+// that the eight lanes adding sums of the same offset within their 16-input
+// chunk hit eight consecutive words (no bank conflicts)
+__device__ __forceinline__ int sum_slot(int n) { return (n & 15) * 8 + (n >> 4); }
+
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map, uint32_t bar,
                                             int x, int y, int z)
 {
@@ -150,6 +192,14 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap *map
         " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
         "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
         : "memory");
+}
+
+__device__ __forceinline__ void tma_prefetch_3d(const CUtensorMap *map, int x, int y, int z)
+{
+    asm volatile("cp.async.bulk.prefetch.tensor.3d.L2.global.tile [%0, {%1, %2, %3}];" ::"l"(
+                     reinterpret_cast<uint64_t>(map)),
+                 "r"(x), "r"(y), "r"(z)
+                 : "memory");
 }
 
 __device__ __forceinline__ uint64_t smem_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo)
@@ -282,15 +332,23 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            int issued[kPackedStages];            // parity of the last load issued into each slot, or -1
-            for (int k = 0; k < kPackedStages; ++k) issued[k] = -1;
+            uint32_t issued = 0, issued_phase = 0;   // per slot: a load was issued / its parity
             bool ok = true;
+            const int per_chan = (p.n_tiles * (p.n_tiles + 1)) / 2;
             for (int item = first_item; ok && item < p.n_items; item += item_step) {
-                const int f = item / ((p.n_tiles * (p.n_tiles + 1)) / 2);
+                const int f = item / per_chan;
                 int I, J;
-                item_tiles(item % ((p.n_tiles * (p.n_tiles + 1)) / 2), I, J);
+                item_tiles(item % per_chan, I, J);
                 const bool diag = I == J;
+                for (int s = 0; s < kPrefetchStages && s < p.n_stages; ++s) {
+                    tma_prefetch_3d(&tmap, J * kTile, f, s * kTc);
+                    if (!diag) tma_prefetch_3d(&tmap, I * kTile, f, s * kTc);
+                }
                 for (int s = 0; s < p.n_stages; ++s) {
+                    if (s + kPrefetchStages < p.n_stages) {
+                        tma_prefetch_3d(&tmap, J * kTile, f, (s + kPrefetchStages) * kTc);
+                        if (!diag) tma_prefetch_3d(&tmap, I * kTile, f, (s + kPrefetchStages) * kTc);
+                    }
                     if (!mbar_wait(bar_packed_empty(stage), phase ^ 1u, abort, p.status, 1)) {
                         ok = false;
                         break;
@@ -300,7 +358,8 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                     mbar_expect_tx(full, diag ? kPackedTileBytes : 2 * kPackedTileBytes);
                     tma_load_3d(dst + kPackedTileBytes, &tmap, full, J * kTile, f, s * kTc);
                     if (!diag) tma_load_3d(dst, &tmap, full, I * kTile, f, s * kTc);
-                    issued[stage] = int(phase);
+                    issued |= 1u << stage;
+                    issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
                     if (++stage == kPackedStages) {
                         stage = 0;
                         phase ^= 1u;
@@ -309,9 +368,9 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
             }
             // every issued load must have landed before the CTA may exit
             for (int k = 0; k < kPackedStages; ++k) {
-                if (issued[k] < 0) continue;
+                if (!((issued >> k) & 1u)) continue;
                 const long long t0 = clock64();
-                while (!mbar_try(bar_packed_full(k), uint32_t(issued[k])) && clock64() - t0 < kWaitLimit) {
+                while (!mbar_try(bar_packed_full(k), (issued_phase >> k) & 1u) && clock64() - t0 < kWaitLimit) {
                 }
             }
         }
@@ -320,7 +379,7 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
         if (lane == 0) {
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t acc_phase[2] = {0, 0};
+            uint32_t acc_phase = 0;                  // bit b: phase of accumulator buffer b
             int local = 0;
             bool ok = true;
             for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
@@ -328,11 +387,11 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                 item_tiles(item % ((p.n_tiles * (p.n_tiles + 1)) / 2), I, J);
                 const bool diag = I == J;
                 const int buf = local & 1;
-                if (!mbar_wait(bar_acc_empty(buf), acc_phase[buf] ^ 1u, abort, p.status, 2)) {
+                if (!mbar_wait(bar_acc_empty(buf), ((acc_phase >> buf) & 1u) ^ 1u, abort, p.status, 2)) {
                     ok = false;
                     break;
                 }
-                acc_phase[buf] ^= 1u;
+                acc_phase ^= 1u << buf;
                 fence_after();
                 const uint32_t d_tmem = tmem + uint32_t(buf * 256);
                 uint32_t accum = 0;
@@ -371,20 +430,22 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
         }
     } else if (warp < kFirstEpiWarp) {
         // ----------------------------------------------------- converters --
-        const int ct = threadIdx.x - kFirstConvWarp * 32;        // 0..255
-        const int c = ct & 7, r0 = ct >> 3;                       // chunk column, first row
+        // thread ct owns chunk column c (16 inputs) of one row (sample) of each
+        // stage, for both tiles, so its per-input sums never leave registers
+        const int ct = threadIdx.x - kFirstConvWarp * 32;        // 0..511
+        const int c = ct & 7, row = ct >> 3;                      // chunk column, row 0..63
         const bool zi = p.zero_invalid != 0;
+        const uint32_t so = uint32_t(row * 128 + ((c ^ (row & 7)) << 4));   // swizzled plane offset
+        const uint32_t po = uint32_t(row * 128 + c * 16);                   // packed offset
         int pstage = 0, cstage = 0;
-        uint32_t pphase = 0, cphase = 0;
-        uint32_t sphase[2] = {0, 0};
+        uint32_t pphase = 0, cphase = 0, sphase = 0;
         int local = 0;
         bool ok = true;
         for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
             int I, J;
             item_tiles(item % ((p.n_tiles * (p.n_tiles + 1)) / 2), I, J);
             const bool diag = I == J;
-            // per-input code sums of this thread's 16 inputs (4 words x 4 bytes):
-            // byte lanes (<= 16 rows) then 16-bit lanes
+            // per-input code sums: byte lanes (<= 16 rows), then 16-bit lanes
             uint32_t b8[2][2][4], s16lo[2][2][4], s16hi[2][2][4];
 #pragma unroll
             for (int t = 0; t < 2; ++t)
@@ -400,40 +461,35 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                 }
                 const uint8_t *pk = smem + kSmPacked + pstage * kPackedStageBytes;
                 uint8_t *pl = smem + kSmPlanes + cstage * kPlaneStageBytes;
+                const uint4 wj = *reinterpret_cast<const uint4 *>(pk + kPackedTileBytes + po);
+                uint4 wi = make_uint4(0u, 0u, 0u, 0u);
+                if (!diag) wi = *reinterpret_cast<const uint4 *>(pk + po);
+                {
+                    const uint32_t ww[4] = {wj.x, wj.y, wj.z, wj.w};
+                    uint32_t R[4], M[4];
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int row = r0 + 32 * h;
-                    const uint32_t so = uint32_t(row * 128 + ((c ^ (row & 7)) << 4));
-                    // J tile: planes M, R, nM
-                    {
-                        const uint4 w = *reinterpret_cast<const uint4 *>(pk + kPackedTileBytes + row * 128 + c * 16);
-                        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-                        uint32_t R[4], M[4];
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            codes(ww[k], zi, R[k], M[k]);
-                            b8[1][0][k] += R[k];
-                            b8[1][1][k] += M[k];
-                        }
-                        *reinterpret_cast<uint4 *>(pl + kOffMJ + so) = make_uint4(M[0], M[1], M[2], M[3]);
-                        *reinterpret_cast<uint4 *>(pl + kOffRJ + so) = make_uint4(R[0], R[1], R[2], R[3]);
-                        *reinterpret_cast<uint4 *>(pl + kOffNMJ + so) =
-                            make_uint4(M[0] | 0x80808080u, M[1] | 0x80808080u, M[2] | 0x80808080u,
-                                       M[3] | 0x80808080u);
+                    for (int k = 0; k < 4; ++k) {
+                        codes(ww[k], zi, R[k], M[k]);
+                        b8[1][0][k] += R[k];
+                        b8[1][1][k] += M[k];
                     }
-                    if (!diag) {
-                        const uint4 w = *reinterpret_cast<const uint4 *>(pk + row * 128 + c * 16);
-                        const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
-                        uint32_t R[4], M[4];
+                    *reinterpret_cast<uint4 *>(pl + kOffMJ + so) = make_uint4(M[0], M[1], M[2], M[3]);
+                    *reinterpret_cast<uint4 *>(pl + kOffRJ + so) = make_uint4(R[0], R[1], R[2], R[3]);
+                    *reinterpret_cast<uint4 *>(pl + kOffNMJ + so) =
+                        make_uint4(M[0] | 0x80808080u, M[1] | 0x80808080u, M[2] | 0x80808080u,
+                                   M[3] | 0x80808080u);
+                }
+                if (!diag) {
+                    const uint32_t ww[4] = {wi.x, wi.y, wi.z, wi.w};
+                    uint32_t R[4], M[4];
 #pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            codes(ww[k], zi, R[k], M[k]);
-                            b8[0][0][k] += R[k];
-                            b8[0][1][k] += M[k];
-                        }
-                        *reinterpret_cast<uint4 *>(pl + kOffRI + so) = make_uint4(R[0], R[1], R[2], R[3]);
-                        *reinterpret_cast<uint4 *>(pl + kOffMI + so) = make_uint4(M[0], M[1], M[2], M[3]);
+                    for (int k = 0; k < 4; ++k) {
+                        codes(ww[k], zi, R[k], M[k]);
+                        b8[0][0][k] += R[k];
+                        b8[0][1][k] += M[k];
                     }
+                    *reinterpret_cast<uint4 *>(pl + kOffRI + so) = make_uint4(R[0], R[1], R[2], R[3]);
+                    *reinterpret_cast<uint4 *>(pl + kOffMI + so) = make_uint4(M[0], M[1], M[2], M[3]);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
@@ -449,8 +505,8 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                     cstage = 0;
                     cphase ^= 1u;
                 }
-                // byte lanes hold at most 16 rows of codes <= 15 (255): widen every 8 stages
-                if ((s & 7) == 7 || s + 1 == p.n_stages) {
+                // byte lanes hold at most 16 rows of codes <= 15 (240): widen every 16 stages
+                if ((s & 15) == 15 || s + 1 == p.n_stages) {
 #pragma unroll
                     for (int t = 0; t < 2; ++t)
 #pragma unroll
@@ -464,28 +520,44 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                 }
             }
             if (!ok) break;
-            // hand the per-input sums of this item to the epilogue
-            const int buf = local & 1;
-            if (!mbar_wait(bar_sums_empty(buf), sphase[buf] ^ 1u, abort, p.status, 6)) {
-                ok = false;
-                break;
-            }
-            sphase[buf] ^= 1u;
-            int *sb = sums + buf * (2 * kTile * 2);
+            // reduce over the four lanes of this warp that share chunk column c
+            // (16-bit lanes stay below 4 x 512 x 15 < 2^16), then hand the
+            // per-input sums of this item to the epilogue
 #pragma unroll
-            for (int t = 0; t < 2; ++t) {
-                if (t == 0 && diag) continue;
+            for (int t = 0; t < 2; ++t)
 #pragma unroll
                 for (int q = 0; q < 2; ++q)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        const int n0 = c * 16 + 4 * k;
-                        int *dst = sb + (t * kTile + n0) * 2 + q;
-                        atomicAdd(dst + 0, int(s16lo[t][q][k] & 0xFFFFu));
-                        atomicAdd(dst + 2, int(s16hi[t][q][k] & 0xFFFFu));
-                        atomicAdd(dst + 4, int(s16lo[t][q][k] >> 16));
-                        atomicAdd(dst + 6, int(s16hi[t][q][k] >> 16));
+                        s16lo[t][q][k] += __shfl_xor_sync(0xFFFFFFFFu, s16lo[t][q][k], 8);
+                        s16lo[t][q][k] += __shfl_xor_sync(0xFFFFFFFFu, s16lo[t][q][k], 16);
+                        s16hi[t][q][k] += __shfl_xor_sync(0xFFFFFFFFu, s16hi[t][q][k], 8);
+                        s16hi[t][q][k] += __shfl_xor_sync(0xFFFFFFFFu, s16hi[t][q][k], 16);
                     }
+            const int buf = local & 1;
+            if (!warp_wait(bar_sums_empty(buf), ((sphase >> buf) & 1u) ^ 1u, abort, p.status, 6, lane, 64)) {
+                ok = false;
+                break;
+            }
+            sphase ^= 1u << buf;
+            if (lane < 8) {
+                int *sb = sums + buf * (2 * 2 * kTile);
+#pragma unroll
+                for (int t = 0; t < 2; ++t) {
+                    if (t == 0 && diag) continue;
+#pragma unroll
+                    for (int q = 0; q < 2; ++q) {
+                        int *row_sums = sb + (t * 2 + q) * kTile;
+#pragma unroll
+                        for (int k = 0; k < 4; ++k) {
+                            const int n0 = c * 16 + 4 * k;
+                            atomicAdd(row_sums + sum_slot(n0 + 0), int(s16lo[t][q][k] & 0xFFFFu));
+                            atomicAdd(row_sums + sum_slot(n0 + 1), int(s16hi[t][q][k] & 0xFFFFu));
+                            atomicAdd(row_sums + sum_slot(n0 + 2), int(s16lo[t][q][k] >> 16));
+                            atomicAdd(row_sums + sum_slot(n0 + 3), int(s16hi[t][q][k] >> 16));
+                        }
+                    }
+                }
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_sums_full(buf));
@@ -493,35 +565,37 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
     } else {
         // ------------------------------------------------------- epilogue --
         const int q = warp & 3;                      // TMEM lane quarter of this warp
-        uint32_t aphase[2] = {0, 0};
+        uint32_t aphase = 0;                          // bit b: phase of buffer b
         int local = 0;
         bool ok = true;
         const long long P = n_pairs(p.n);
         const int T_eff = p.n_stages * kTc;
+        const int per_chan = (p.n_tiles * (p.n_tiles + 1)) / 2;
         for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
-            const int f = item / ((p.n_tiles * (p.n_tiles + 1)) / 2);
+            const int f = item / per_chan;
             int I, J;
-            item_tiles(item % ((p.n_tiles * (p.n_tiles + 1)) / 2), I, J);
+            item_tiles(item % per_chan, I, J);
             const bool diag = I == J;
             const int buf = local & 1;
             // the four epilogue warps decide together whether to go on, so that
             // none of them is ever left waiting at a named barrier
-            const bool mine = mbar_wait(bar_acc_full(buf), aphase[buf], abort, p.status, 7) &&
-                              mbar_wait(bar_sums_full(buf), aphase[buf], abort, p.status, 8);
+            const uint32_t ph = (aphase >> buf) & 1u;
+            const bool mine = warp_wait(bar_acc_full(buf), ph, abort, p.status, 7, lane, 256) &&
+                              warp_wait(bar_sums_full(buf), ph, abort, p.status, 8, lane, 64);
             if (lane == 0) epi_ok[q] = mine ? 1 : 0;
             named_sync(2, kEpiWarps * 32);
             ok = epi_ok[0] && epi_ok[1] && epi_ok[2] && epi_ok[3];
             named_sync(2, kEpiWarps * 32);
             if (!ok) break;
-            aphase[buf] ^= 1u;
+            aphase ^= 1u << buf;
             fence_after();
-            int *sb = sums + buf * (2 * kTile * 2);
-            const int *si = sb + (diag ? kTile : 0) * 2;      // I tile sums
-            const int *sj = sb + kTile * 2;                    // J tile sums
+            int *sb = sums + buf * (2 * 2 * kTile);
+            const int *si = sb + (diag ? 1 : 0) * 2 * kTile;     // I tile sums: [r/m][slot]
+            const int *sj = sb + 1 * 2 * kTile;                   // J tile sums
             const int il = q * 32 + lane;
             const int i = I * kTile + il;
-            const int Ei = si[il * 2] + si[il * 2 + 1];
-            const int Di = si[il * 2 + 1] - si[il * 2];
+            const int Sri = si[sum_slot(il)], Smi = si[kTile + sum_slot(il)];
+            const int Ei = Sri + Smi, Di = Smi - Sri;
             const int base_re = 128 * T_eff - 8 * Ei;
             int32_t *out = p.acc + ((size_t)f * P + (size_t)i * (i + 1) / 2) * 2;
             const uint32_t taddr = tmem + uint32_t(buf * 256) + (uint32_t(q * 32) << 16);
@@ -537,12 +611,11 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                         const int jl = c0 + k;
                         const int j = J * kTile + jl;
                         if (j > i) break;
-                        const int Ej = sj[jl * 2] + sj[jl * 2 + 1];
-                        const int Dj = sj[jl * 2 + 1] - sj[jl * 2];
+                        const int Srj = sj[sum_slot(jl)], Smj = sj[kTile + sum_slot(jl)];
                         const int pre = __float2int_rn(__uint_as_float(vre[k]) * 262144.0f);
                         const int pim = __float2int_rn(__uint_as_float(vim[k]) * 262144.0f);
-                        const int re = pre + base_re - 8 * Ej;
-                        const int im = pim - 8 * Di + 8 * Dj;
+                        const int re = pre + base_re - 8 * (Srj + Smj);
+                        const int im = pim - 8 * Di + 8 * (Smj - Srj);
                         int2 *dst = reinterpret_cast<int2 *>(out + size_t(j) * 2);
                         if (p.fresh) {
                             *dst = make_int2(re, im);
@@ -559,7 +632,7 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
             // every epilogue warp has read this item's sums: clear them for the
             // item that reuses the buffer, then release TMEM and sums
             named_sync(2, kEpiWarps * 32);
-            for (int e = threadIdx.x - kFirstEpiWarp * 32; e < 2 * kTile * 2; e += kEpiWarps * 32) sb[e] = 0;
+            for (int e = threadIdx.x - kFirstEpiWarp * 32; e < 2 * 2 * kTile; e += kEpiWarps * 32) sb[e] = 0;
             __syncwarp();
             if (lane == 0) {
                 mbar_arrive(bar_acc_empty(buf));
