@@ -104,6 +104,10 @@ int corr_destroy(corr_ctx *ctx);
  * else CORR_E_STATE.  The default is CORR_PATH_AUTO. */
 int corr_set_path(corr_ctx *ctx, int path);
 
+/* Tile of the CUDA-core path: 32 or 64 inputs per side, or 0 to choose by
+ * shape (32 when n_inputs <= 32).  Only between integrations (CORR_E_STATE). */
+int corr_set_tile(corr_ctx *ctx, int tile);
+
 /* The path that accumulate calls will run (AUTO resolved). */
 int corr_get_path(const corr_ctx *ctx);
 
@@ -183,6 +187,73 @@ int corr_set_state(corr_ctx *ctx, const void *h_buf, size_t bytes, void *stream)
  */
 int corr_unpack(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs,
                 int8_t *d_out, unsigned flags, void *stream);
+
+/* ------------------------------------------------------------------- batch -- */
+
+/*
+ * Several arrays of uneven size correlated together (the MWA correlator runs
+ * one X-engine per GPU over a fixed set of channels, Section 3.4; here one
+ * GPU serves several arrays).  Arrays on the tensor-core path are correlated
+ * by ONE persistent launch (up to CORR_BATCH_TC_GROUP arrays per launch; the
+ * work items of all of them, longest first, shared by every SM); arrays on
+ * other paths get their own kernels on the same stream.
+ */
+#define CORR_BATCH_MAX 16
+#define CORR_BATCH_TC_GROUP 4
+
+typedef struct corr_array_desc {
+    int n_inputs;        /* N */
+    int n_chan;          /* F */
+    int n_time_per_int;  /* samples per integration (cap) */
+    int path;            /* CORR_PATH_* for this array; AUTO picks per shape */
+    unsigned flags;      /* CORR_ZERO_INVALID or 0 */
+    int tile;            /* CUDA-core tile (corr_set_tile), 0 = by shape */
+} corr_array_desc;
+
+typedef struct corr_batch corr_batch;
+
+/* NULL on error (corr_last_error): CORR_E_ARG for n_arrays outside
+ * [1, CORR_BATCH_MAX] or an invalid descriptor (same rules as corr_create),
+ * CORR_E_UNSUPPORTED if a requested path cannot run its shape. */
+corr_batch *corr_batch_create(int n_arrays, const corr_array_desc *descs);
+int corr_batch_destroy(corr_batch *b);
+
+/* Device workspace for all arrays (one caller-owned, 256-byte aligned block). */
+size_t corr_batch_workspace_bytes(const corr_batch *b);
+int corr_batch_bind_workspace(corr_batch *b, void *d_ws, size_t bytes);
+
+/* Resolved path of array a (CORR_PATH_*), or a negative status. */
+int corr_batch_path(const corr_batch *b, int a);
+
+/* Samples in array a's running integration. */
+long long corr_batch_samples(const corr_batch *b, int a);
+
+/*
+ * Accumulate d_volt[a] (device, [n_time[a]][F_a][N_a]) into array a for every
+ * a with d_volt[a] != NULL and n_time[a] > 0.  All checks happen before
+ * anything is enqueued: CORR_E_OVERFLOW if any array would exceed its cap.
+ */
+int corr_batch_accumulate(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
+                          void *stream);
+
+/* Dump every array a with d_vis[a] != NULL (device int32 [F_a][P_a][2]). */
+int corr_batch_dump(corr_batch *b, int32_t *const *d_vis, void *stream);
+
+/* corr_sync for every array of the batch. */
+int corr_batch_sync(corr_batch *b, void *stream);
+
+/*
+ * Capture one whole integration -- corr_batch_accumulate(d_volt, n_time)
+ * followed by corr_batch_dump(d_vis) -- into an executable CUDA graph
+ * (returned as an opaque handle in *graph_exec).  The batch must be between
+ * integrations (every array at 0 samples, else CORR_E_STATE) and stays so:
+ * each corr_graph_launch replays the full integration on the captured
+ * buffers.  `stream` must not be the legacy default stream (CORR_E_ARG).
+ */
+int corr_batch_graph_capture(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
+                             int32_t *const *d_vis, void *stream, void **graph_exec);
+int corr_graph_launch(void *graph_exec, void *stream);
+int corr_graph_destroy(void *graph_exec);
 
 /* ------------------------------------------------------- no device allocation -- */
 

@@ -50,6 +50,15 @@ class Profile(ctypes.Structure):
                                 "ms": float(self.ms[k])} for k in range(4)}
 
 
+class ArrayDesc(ctypes.Structure):
+    _fields_ = [("n_inputs", ctypes.c_int), ("n_chan", ctypes.c_int),
+                ("n_time_per_int", ctypes.c_int), ("path", ctypes.c_int), ("flags", ctypes.c_uint),
+                ("tile", ctypes.c_int)]
+
+
+BATCH_MAX = 16
+
+
 class CorrError(RuntimeError):
     def __init__(self, status: int, what: str):
         self.status = status
@@ -82,6 +91,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_destroy": ([vp], c_int),
             "corr_set_path": ([vp, c_int], c_int),
             "corr_get_path": ([vp], c_int),
+            "corr_set_tile": ([vp, c_int], c_int),
             "corr_set_flags": ([vp, ctypes.c_uint], c_int),
             "corr_workspace_bytes": ([vp], c_size),
             "corr_bind_workspace": ([vp, vp, c_size], c_int),
@@ -96,6 +106,19 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_set_state": ([vp, vp, c_size, vp], c_int),
             "corr_unpack": ([vp, c_int, c_int, c_int, vp, ctypes.c_uint, vp], c_int),
             "corr_xmac_noalloc": ([vp, c_int, c_int, c_int, vp, ctypes.c_uint, vp], c_int),
+            "corr_batch_create": ([c_int, ctypes.POINTER(ArrayDesc)], vp),
+            "corr_batch_destroy": ([vp], c_int),
+            "corr_batch_workspace_bytes": ([vp], c_size),
+            "corr_batch_bind_workspace": ([vp, vp, c_size], c_int),
+            "corr_batch_path": ([vp, c_int], c_int),
+            "corr_batch_samples": ([vp, c_int], ctypes.c_longlong),
+            "corr_batch_accumulate": ([vp, ctypes.POINTER(vp), ctypes.POINTER(c_int), vp], c_int),
+            "corr_batch_dump": ([vp, ctypes.POINTER(vp), vp], c_int),
+            "corr_batch_sync": ([vp, vp], c_int),
+            "corr_batch_graph_capture": ([vp, ctypes.POINTER(vp), ctypes.POINTER(c_int),
+                                          ctypes.POINTER(vp), vp, ctypes.POINTER(vp)], c_int),
+            "corr_graph_launch": ([vp, vp], c_int),
+            "corr_graph_destroy": ([vp], c_int),
             "corr_profile_enable": ([vp, c_int], c_int),
             "corr_profile_read": ([vp, ctypes.POINTER(Profile), c_int], c_int),
             "corr_last_error": ([], c_int),
@@ -181,6 +204,10 @@ class Correlator:
     @property
     def path(self) -> str:
         return PATH_NAMES[self._lib.corr_get_path(self._ctx)]
+
+    def set_tile(self, tile: int) -> None:
+        """CUDA-core tile: 32, 64 or 0 (by shape)."""
+        _check(self._lib.corr_set_tile(self._ctx, int(tile)), f"corr_set_tile({tile})")
 
     def set_path(self, path: str | int) -> None:
         code = PATHS[path] if isinstance(path, str) else int(path)
@@ -272,6 +299,141 @@ class Correlator:
 
     def __exit__(self, *exc):
         self.close()
+
+
+class Graph:
+    """An executable CUDA graph holding one whole integration of a Batch."""
+
+    def __init__(self, lib, handle, keep):
+        self._lib, self._h, self._keep = lib, handle, keep
+
+    def launch(self, stream=None) -> None:
+        _check(self._lib.corr_graph_launch(self._h, _stream_handle(stream)), "corr_graph_launch")
+
+    def close(self) -> None:
+        if self._h:
+            self._lib.corr_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Several arrays correlated together; tensor-core arrays share one
+    persistent launch.  ``arrays`` holds (n_inputs, n_chan, n_time_per_int)
+    tuples or dicts with those keys plus optional ``path`` / ``zero_invalid``."""
+
+    def __init__(self, arrays, device: torch.device | int | None = None):
+        self._lib = load()
+        specs = []
+        for a in arrays:
+            if isinstance(a, dict):
+                specs.append((a["n_inputs"], a["n_chan"], a["n_time_per_int"],
+                              a.get("path", "auto"), bool(a.get("zero_invalid", False)),
+                              int(a.get("tile", 0))))
+            else:
+                specs.append((a[0], a[1], a[2], "auto", False, 0))
+        self.specs = specs
+        self.device = torch.device("cuda", torch.cuda.current_device() if device is None else
+                                   (device if isinstance(device, int) else device.index or 0))
+        descs = (ArrayDesc * len(specs))()
+        for k, (n, f, t, path, zi, tile) in enumerate(specs):
+            descs[k] = ArrayDesc(n, f, t, PATHS[path] if isinstance(path, str) else int(path),
+                                 ZERO_INVALID if zi else 0, tile)
+        with torch.cuda.device(self.device):
+            h = self._lib.corr_batch_create(len(specs), descs)
+            if not h:
+                raise CorrError(self._lib.corr_last_error(), "corr_batch_create")
+            self._h = ctypes.c_void_p(h)
+            nbytes = self._lib.corr_batch_workspace_bytes(self._h)
+            self._ws = torch.empty(max(nbytes, 1), dtype=torch.uint8, device=self.device)
+            _check(self._lib.corr_batch_bind_workspace(self._h, ctypes.c_void_p(self._ws.data_ptr()),
+                                                       nbytes), "corr_batch_bind_workspace")
+
+    def __len__(self):
+        return len(self.specs)
+
+    @property
+    def paths(self) -> list[str]:
+        return [PATH_NAMES[self._lib.corr_batch_path(self._h, a)] for a in range(len(self))]
+
+    def samples(self, a: int) -> int:
+        return int(self._lib.corr_batch_samples(self._h, a))
+
+    def _ptrs(self, tensors, what):
+        arr = (ctypes.c_void_p * len(self))()
+        for a, t in enumerate(tensors):
+            arr[a] = ctypes.c_void_p(t.data_ptr()) if t is not None else None
+        return arr
+
+    def _volts(self, volts):
+        if len(volts) != len(self):
+            raise ValueError("one voltage tensor (or None) per array")
+        nt = (ctypes.c_int * len(self))()
+        for a, v in enumerate(volts):
+            if v is None:
+                continue
+            n, f = self.specs[a][0], self.specs[a][1]
+            if (v.dtype != torch.uint8 or v.dim() != 3 or not v.is_contiguous() or
+                    v.shape[1] != f or v.shape[2] != n or v.device != self.device):
+                raise ValueError(f"array {a}: voltages must be a contiguous uint8 [T][{f}][{n}] "
+                                 f"tensor on {self.device}")
+            nt[a] = int(v.shape[0])
+        return self._ptrs(volts, "volt"), nt
+
+    def _outs(self, outs):
+        if outs is None:
+            outs = [torch.empty((f, n * (n + 1) // 2, 2), dtype=torch.int32, device=self.device)
+                    for (n, f, *_rest) in self.specs]
+        if len(outs) != len(self):
+            raise ValueError("one output tensor (or None) per array")
+        for a, o in enumerate(outs):
+            n, f = self.specs[a][0], self.specs[a][1]
+            if o is not None and (o.dtype != torch.int32 or o.shape != (f, n * (n + 1) // 2, 2)
+                                  or not o.is_contiguous() or o.device != self.device):
+                raise ValueError(f"array {a}: output must be a contiguous int32 [{f}][P][2] tensor")
+        return outs
+
+    def accumulate(self, volts, stream=None) -> None:
+        ptrs, nt = self._volts(volts)
+        _check(self._lib.corr_batch_accumulate(self._h, ptrs, nt, _stream_handle(stream)),
+               "corr_batch_accumulate")
+
+    def dump(self, outs=None, stream=None):
+        outs = self._outs(outs)
+        _check(self._lib.corr_batch_dump(self._h, self._ptrs(outs, "vis"), _stream_handle(stream)),
+               "corr_batch_dump")
+        return outs
+
+    def sync(self, stream=None) -> None:
+        _check(self._lib.corr_batch_sync(self._h, _stream_handle(stream)), "corr_batch_sync")
+
+    def capture(self, volts, outs=None, stream=None) -> tuple[Graph, list]:
+        """Capture accumulate(volts) + dump(outs) as one replayable graph."""
+        if stream is None:
+            stream = torch.cuda.Stream(self.device)
+        ptrs, nt = self._volts(volts)
+        outs = self._outs(outs)
+        h = ctypes.c_void_p()
+        _check(self._lib.corr_batch_graph_capture(self._h, ptrs, nt, self._ptrs(outs, "vis"),
+                                                  _stream_handle(stream), ctypes.byref(h)),
+               "corr_batch_graph_capture")
+        return Graph(self._lib, h, (list(volts), outs)), outs
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.corr_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
 
 
 def unpack(volt: torch.Tensor, zero_invalid: bool = False, stream=None) -> torch.Tensor:

@@ -25,6 +25,7 @@ struct corr_ctx {
     int n = 0, f = 0, t_max = 0;
     int device = 0, sm_major = 0, sm_minor = 0, sm_count = 0;
     int path = CORR_PATH_AUTO;
+    int tile = 0;            // CUDA-core tile (32 or 64), 0 = chosen by shape
     unsigned flags = 0;
 
     // workspace (caller-owned device memory)
@@ -166,18 +167,20 @@ int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
         const size_t plane_max = size_t(P.f_chunk) * (P.t_chunk / 2) * P.n_pad;
         int32_t *A = reinterpret_cast<int32_t *>(c->stage);
         int32_t *W = A + plane_max;
+        const int tile = c->tile ? c->tile : (c->n <= 32 ? 32 : 64);
+        const int n_pad = int(round_up(size_t(c->n), size_t(tile)));
         for (int t0 = 0; t0 < nt; t0 += P.t_chunk) {
             const int ntc = nt - t0 < P.t_chunk ? nt - t0 : P.t_chunk;
             const int tw_pad = int(round_up(size_t(ntc), 2 * kDp4aKW) / 2);
             for (int f0 = 0; f0 < c->f; f0 += P.f_chunk) {
                 const int fc = c->f - f0 < P.f_chunk ? c->f - f0 : P.f_chunk;
                 prof_begin(c, s);
-                e = launch_unpack_words(volt + size_t(t0) * row, c->f, c->n, f0, fc, ntc, P.n_pad,
+                e = launch_unpack_words(volt + size_t(t0) * row, c->f, c->n, f0, fc, ntc, n_pad,
                                         tw_pad, zi, A, W, s);
                 prof_end(c, CORR_K_UNPACK, s, 1);
                 if (e != cudaSuccess) return cuda_fail(e);
                 prof_begin(c, s);
-                e = launch_xeng_dp4a(A, W, c->n, P.n_pad, fc, tw_pad, c->acc, f0, fresh, s);
+                e = launch_xeng_dp4a(A, W, c->n, n_pad, fc, tw_pad, c->acc, f0, fresh, tile, s);
                 prof_end(c, CORR_K_XENGINE, s, 1);
                 if (e != cudaSuccess) return cuda_fail(e);
             }
@@ -333,6 +336,14 @@ int corr_set_path(corr_ctx *c, int path)
     if (c->samples != 0) return ret(CORR_E_STATE);
     if (!path_supported(c, path)) return ret(CORR_E_UNSUPPORTED);
     c->path = path;
+    return ret(CORR_OK);
+}
+
+int corr_set_tile(corr_ctx *c, int tile)
+{
+    if (!c || (tile != 0 && tile != 32 && tile != 64)) return ret(CORR_E_ARG);
+    if (c->samples != 0) return ret(CORR_E_STATE);
+    c->tile = tile;
     return ret(CORR_OK);
 }
 
@@ -569,6 +580,252 @@ int corr_unpack(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs, int
                                          n_time, (flags & CORR_ZERO_INVALID) != 0, d_out,
                                          nullptr, static_cast<cudaStream_t>(stream));
     return ret(e == cudaSuccess ? CORR_OK : CORR_E_CUDA);
+}
+
+/* ------------------------------------------------------------------- batch */
+
+}  // extern "C"
+
+struct corr_batch {
+    int n = 0;
+    corr_ctx *ctx[CORR_BATCH_MAX] = {};
+    size_t ws_off[CORR_BATCH_MAX] = {};
+    size_t ws_bytes[CORR_BATCH_MAX] = {};
+    size_t total = 0;
+    bool bound = false;
+};
+
+extern "C" {
+
+corr_batch *corr_batch_create(int n_arrays, const corr_array_desc *descs)
+{
+    if (n_arrays < 1 || n_arrays > CORR_BATCH_MAX || !descs) {
+        ret(CORR_E_ARG);
+        return nullptr;
+    }
+    corr_batch *b = new (std::nothrow) corr_batch();
+    if (!b) {
+        ret(CORR_E_NOMEM);
+        return nullptr;
+    }
+    for (int a = 0; a < n_arrays; ++a) {
+        const corr_array_desc &d = descs[a];
+        corr_ctx *c = corr_create(d.n_inputs, d.n_chan, d.n_time_per_int);
+        int rc = c ? CORR_OK : corr_last_error();
+        if (rc == CORR_OK) rc = corr_set_flags(c, d.flags);
+        if (rc == CORR_OK) rc = corr_set_path(c, d.path);
+        if (rc == CORR_OK) rc = corr_set_tile(c, d.tile);
+        if (rc != CORR_OK) {
+            if (c) corr_destroy(c);
+            b->n = a;
+            corr_batch_destroy(b);
+            ret(rc);
+            return nullptr;
+        }
+        b->ctx[a] = c;
+        b->ws_off[a] = b->total;
+        b->ws_bytes[a] = corr_workspace_bytes(c);
+        b->total = round_up(b->total + b->ws_bytes[a], kAlign);
+    }
+    b->n = n_arrays;
+    ret(CORR_OK);
+    return b;
+}
+
+int corr_batch_destroy(corr_batch *b)
+{
+    if (!b) return ret(CORR_E_ARG);
+    for (int a = 0; a < b->n; ++a)
+        if (b->ctx[a]) corr_destroy(b->ctx[a]);
+    delete b;
+    return ret(CORR_OK);
+}
+
+size_t corr_batch_workspace_bytes(const corr_batch *b)
+{
+    if (!b) {
+        ret(CORR_E_ARG);
+        return 0;
+    }
+    g_last_error = CORR_OK;
+    return b->total;
+}
+
+int corr_batch_bind_workspace(corr_batch *b, void *d_ws, size_t bytes)
+{
+    if (!b || !d_ws || (reinterpret_cast<uintptr_t>(d_ws) % kAlign) != 0 || bytes < b->total)
+        return ret(CORR_E_ARG);
+    for (int a = 0; a < b->n; ++a) {
+        const int rc = corr_bind_workspace(b->ctx[a], static_cast<uint8_t *>(d_ws) + b->ws_off[a],
+                                           b->ws_bytes[a]);
+        if (rc != CORR_OK) return ret(rc);
+    }
+    b->bound = true;
+    return ret(CORR_OK);
+}
+
+int corr_batch_path(const corr_batch *b, int a)
+{
+    if (!b || a < 0 || a >= b->n) return ret(CORR_E_ARG);
+    return corr_get_path(b->ctx[a]);
+}
+
+long long corr_batch_samples(const corr_batch *b, int a)
+{
+    if (!b || a < 0 || a >= b->n) {
+        ret(CORR_E_ARG);
+        return -1;
+    }
+    return corr_samples(b->ctx[a]);
+}
+
+int corr_batch_accumulate(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
+                          void *stream)
+{
+    if (!b || !d_volt || !n_time) return ret(CORR_E_ARG);
+    if (!b->bound) return ret(CORR_E_STATE);
+    // every check before anything is enqueued
+    for (int a = 0; a < b->n; ++a) {
+        if (n_time[a] < 0) return ret(CORR_E_ARG);
+        if (!d_volt[a] || n_time[a] == 0) continue;
+        if (b->ctx[a]->samples + n_time[a] > b->ctx[a]->t_max) return ret(CORR_E_OVERFLOW);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    // tensor-core arrays: one persistent launch per group of up to
+    // CORR_BATCH_TC_GROUP arrays and per kTcMaxSamples samples
+    int tc[CORR_BATCH_MAX], n_tc = 0, max_nt = 0;
+    for (int a = 0; a < b->n; ++a) {
+        if (!d_volt[a] || n_time[a] == 0) continue;
+        if (resolve_path(b->ctx[a], b->ctx[a]->path) == CORR_PATH_TC_FP8) {
+            tc[n_tc++] = a;
+            if (n_time[a] > max_nt) max_nt = n_time[a];
+        }
+    }
+    for (int g0 = 0; g0 < n_tc; g0 += CORR_BATCH_TC_GROUP) {
+        const int gn = n_tc - g0 < CORR_BATCH_TC_GROUP ? n_tc - g0 : CORR_BATCH_TC_GROUP;
+        corr_ctx *lead = b->ctx[tc[g0]];
+        for (int t0 = 0; t0 < max_nt; t0 += kTcMaxSamples) {
+            TcArray arr[CORR_BATCH_TC_GROUP];
+            int k = 0;
+            for (int x = 0; x < gn; ++x) {
+                corr_ctx *c = b->ctx[tc[g0 + x]];
+                const int nt = n_time[tc[g0 + x]];
+                const int ntc = nt - t0 <= 0 ? 0 : (nt - t0 < kTcMaxSamples ? nt - t0 : kTcMaxSamples);
+                arr[k].volt = d_volt[tc[g0 + x]] + size_t(t0 > nt ? nt : t0) * size_t(c->f) * size_t(c->n);
+                arr[k].acc = c->acc;
+                arr[k].n_chan = c->f;
+                arr[k].n = c->n;
+                arr[k].nt = ntc;
+                arr[k].zero_invalid = (c->flags & CORR_ZERO_INVALID) != 0;
+                arr[k].fresh = t0 == 0 ? c->fresh : false;
+                ++k;
+            }
+            prof_begin(lead, s);
+            cudaError_t e = launch_xeng_tc_batch(arr, k, lead->status, s);
+            prof_end(lead, CORR_K_XENGINE, s, 1);
+            if (e != cudaSuccess) return ret(cuda_fail(e));
+        }
+        for (int x = 0; x < gn; ++x) {
+            corr_ctx *c = b->ctx[tc[g0 + x]];
+            c->fresh = false;
+            c->samples += n_time[tc[g0 + x]];
+        }
+    }
+    // every other array on its own kernels
+    for (int a = 0; a < b->n; ++a) {
+        if (!d_volt[a] || n_time[a] == 0) continue;
+        if (resolve_path(b->ctx[a], b->ctx[a]->path) == CORR_PATH_TC_FP8) continue;
+        const int rc = accumulate_device(b->ctx[a], d_volt[a], n_time[a], s);
+        if (rc != CORR_OK) return ret(rc);
+        b->ctx[a]->samples += n_time[a];
+    }
+    return ret(CORR_OK);
+}
+
+int corr_batch_dump(corr_batch *b, int32_t *const *d_vis, void *stream)
+{
+    if (!b || !d_vis) return ret(CORR_E_ARG);
+    if (!b->bound) return ret(CORR_E_STATE);
+    for (int a = 0; a < b->n; ++a) {
+        if (!d_vis[a]) continue;
+        const int rc = corr_dump(b->ctx[a], d_vis[a], stream);
+        if (rc != CORR_OK) return ret(rc);
+    }
+    return ret(CORR_OK);
+}
+
+int corr_batch_sync(corr_batch *b, void *stream)
+{
+    if (!b) return ret(CORR_E_ARG);
+    int first = CORR_OK;
+    for (int a = 0; a < b->n; ++a) {
+        const int rc = corr_sync(b->ctx[a], stream);
+        if (rc != CORR_OK && first == CORR_OK) first = rc;
+    }
+    return ret(first);
+}
+
+int corr_batch_graph_capture(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
+                             int32_t *const *d_vis, void *stream, void **graph_exec)
+{
+    if (!b || !d_volt || !n_time || !d_vis || !graph_exec || !stream) return ret(CORR_E_ARG);
+    if (!b->bound) return ret(CORR_E_STATE);
+    for (int a = 0; a < b->n; ++a)
+        if (b->ctx[a]->samples != 0) return ret(CORR_E_STATE);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    *graph_exec = nullptr;
+    // capture never records timing events
+    bool prof[CORR_BATCH_MAX];
+    for (int a = 0; a < b->n; ++a) {
+        prof[a] = b->ctx[a]->prof_on;
+        b->ctx[a]->prof_on = false;
+    }
+    if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+        cudaGetLastError();
+        for (int a = 0; a < b->n; ++a) b->ctx[a]->prof_on = prof[a];
+        return ret(CORR_E_CUDA);
+    }
+    int rc = corr_batch_accumulate(b, d_volt, n_time, stream);
+    if (rc == CORR_OK) rc = corr_batch_dump(b, d_vis, stream);
+    cudaGraph_t graph = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(s, &graph);
+    for (int a = 0; a < b->n; ++a) {
+        b->ctx[a]->prof_on = prof[a];
+        b->ctx[a]->samples = 0;       // the captured integration ends with its dump
+        b->ctx[a]->fresh = true;
+    }
+    if (rc != CORR_OK || e != cudaSuccess || !graph) {
+        cudaGetLastError();
+        if (graph) cudaGraphDestroy(graph);
+        return ret(rc != CORR_OK ? rc : CORR_E_CUDA);
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess) {
+        cudaGetLastError();
+        return ret(CORR_E_CUDA);
+    }
+    *graph_exec = exec;
+    return ret(CORR_OK);
+}
+
+int corr_graph_launch(void *graph_exec, void *stream)
+{
+    if (!graph_exec) return ret(CORR_E_ARG);
+    if (cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph_exec), static_cast<cudaStream_t>(stream)) !=
+        cudaSuccess) {
+        cudaGetLastError();
+        return ret(CORR_E_CUDA);
+    }
+    return ret(CORR_OK);
+}
+
+int corr_graph_destroy(void *graph_exec)
+{
+    if (!graph_exec) return ret(CORR_E_ARG);
+    cudaGraphExecDestroy(static_cast<cudaGraphExec_t>(graph_exec));
+    return ret(CORR_OK);
 }
 
 int corr_profile_enable(corr_ctx *c, int on)

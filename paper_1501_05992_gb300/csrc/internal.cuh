@@ -18,6 +18,7 @@ constexpr int kMmaKT = 64;             // samples per K stage of the mma.sync ke
 constexpr size_t kStageCap = size_t(1) << 30;  // unpacked-operand staging cap, bytes
 constexpr int kHostChunk = 500;        // samples per host->device transfer chunk
 constexpr int kTcMaxSamples = 32768;   // tcgen05 path: samples per launch (FP32 sums < 2^24)
+constexpr int kTcMaxArrays = 4;        // tcgen05 path: arrays correlated by one launch
 constexpr size_t kAlign = 256;
 
 __host__ __device__ inline long long n_pairs(long long n) { return n * (n + 1) / 2; }
@@ -64,9 +65,10 @@ cudaError_t launch_unpack_kmajor(const uint8_t *volt, int n_chan, int n, int f0,
                                  int8_t *out, int8_t *out_tw, cudaStream_t s);
 
 // CUDA-core X-engine over a staged channel chunk; adds (or, if `fresh`,
-// stores) into acc[f0 + fl][P][2].
+// stores) into acc[f0 + fl][P][2].  tile: 32 or 64 inputs per side (n_pad a
+// multiple of it).
 cudaError_t launch_xeng_dp4a(const int32_t *A, const int32_t *W, int n, int n_pad, int fc,
-                             int tw_pad, int32_t *acc, int f0, bool fresh, cudaStream_t s);
+                             int tw_pad, int32_t *acc, int f0, bool fresh, int tile, cudaStream_t s);
 
 // int8 mma.sync X-engine over a staged K-major channel chunk (X and its
 // twisted plane Xt, both [fc][n_pad][t_pad][2]).
@@ -75,6 +77,16 @@ cudaError_t launch_xeng_mma8(const int8_t *X, const int8_t *Xt, int n, int n_pad
 
 // tcgen05 FP8 X-engine straight from packed voltages (no staging).
 bool tc_supported(int n_inputs, int device);
+struct TcArray {
+    const uint8_t *volt;   // [nt][n_chan][n] packed voltages
+    int32_t *acc;          // [n_chan][P][2] accumulators
+    int n_chan, n, nt;
+    bool zero_invalid, fresh;
+};
+// One persistent launch over every (channel, tile pair) of up to
+// kTcMaxArrays arrays (nt <= kTcMaxSamples each; arrays with nt == 0 skipped).
+cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus *status,
+                                 cudaStream_t s);
 cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool zero_invalid,
                            int32_t *acc, bool fresh, DeviceStatus *status, cudaStream_t s);
 

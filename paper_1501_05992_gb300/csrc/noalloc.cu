@@ -78,7 +78,7 @@ extern "C" int corr_xmac_noalloc(const uint8_t *d_volt, int n_time, int n_chan, 
     const bool zi = (flags & CORR_ZERO_INVALID) != 0;
     if (launch_unpack_words(d_volt, n_chan, n_inputs, 0, n_chan, n_time, n_pad, tw_pad, zi, A, W,
                             s) != cudaSuccess ||
-        launch_xeng_dp4a(A, W, n_inputs, n_pad, n_chan, tw_pad, d_vis, 0, /*fresh=*/true, s) !=
+        launch_xeng_dp4a(A, W, n_inputs, n_pad, n_chan, tw_pad, d_vis, 0, /*fresh=*/true, kDp4aTile, s) !=
             cudaSuccess)
         return set_last_error(CORR_E_CUDA);
     return set_last_error(CORR_OK);

@@ -4,8 +4,8 @@
 // This is the GB300 restatement of the paper's xGPU idea (Section 3.4.2): a
 // thread block owns an m x n tile of baselines and integrates the products
 // over time in registers, which raises the arithmetic intensity to
-// 32mnI / (16(m+n)I + 64mn) (Eq. 4).  Here the tile is 64 x 64 inputs per
-// block, 8 x 4 per thread, and one dp4a instruction performs the four
+// 32mnI / (16(m+n)I + 64mn) (Eq. 4).  Here the tile is 64 x 64 (or 32 x 32)
+// inputs per block, 8 x 4 per thread, and one dp4a instruction performs the four
 // multiply-adds of two samples of one complex product:
 //
 //   a_i = (r_i(t), m_i(t), r_i(t+1), m_i(t+1))      the "words" plane
@@ -16,15 +16,18 @@
 // so Re/Im of V_ij = sum_t x_i conj(x_j) cost one dp4a each per two samples.
 // Operands are staged through shared memory with cp.async double buffering.
 // Only lower-triangle tiles (bj <= bi) are launched; a diagonal tile computes
-// its full square and stores only j <= i.
+// its full square and stores only j <= i.  Two tile shapes: 64 x 64 inputs
+// (128 threads) and 32 x 32 (32 threads, less diagonal waste on small arrays).
 #include "internal.cuh"
 
 namespace corr {
 namespace {
 
-constexpr int T = kDp4aTile;      // 64
 constexpr int KW = kDp4aKW;       // 32 words = 64 samples per stage
-constexpr int kThreads = 128;     // 8 (rows) x 16 (cols) threads, 8x4 each
+// tile T x T inputs per block; each thread owns 8 rows x 4 columns, so a
+// block has (T/8) x (T/4) threads: 128 for T = 64, 32 for T = 32
+template <int T>
+__host__ __device__ constexpr int threads_for() { return (T / 8) * (T / 4); }
 
 __device__ __forceinline__ void cp_async16(void *smem, const void *gmem)
 {
@@ -44,11 +47,13 @@ __device__ __forceinline__ void tile_of(int b, int &bi, int &bj)
     bj = b - i * (i + 1) / 2;
 }
 
-template <bool kFresh>
-__global__ void __launch_bounds__(kThreads, 4)
+template <int T, bool kFresh>
+__global__ void __launch_bounds__(threads_for<T>())
 xeng_dp4a_kernel(const int32_t *__restrict__ A, const int32_t *__restrict__ W, int n,
                  int n_pad, int tw_pad, int32_t *__restrict__ acc, int f0)
 {
+    constexpr int kThreads = threads_for<T>();
+    constexpr int kCols = T / 4;       // threads along j
     __shared__ __align__(16) int32_t sA[2][KW][T];
     __shared__ __align__(16) int32_t sB[2][KW][T];
     __shared__ __align__(16) int32_t sW[2][KW][T];
@@ -58,7 +63,7 @@ xeng_dp4a_kernel(const int32_t *__restrict__ A, const int32_t *__restrict__ W, i
     const int fl = blockIdx.y;
     const int i_base = bi * T, j_base = bj * T;
     const int tid = threadIdx.x;
-    const int tx = tid & 15, ty = tid >> 4;
+    const int tx = tid % kCols, ty = tid / kCols;
 
     const size_t plane = (size_t)fl * tw_pad * n_pad;
     const int32_t *gA = A + plane + i_base;
@@ -140,17 +145,27 @@ xeng_dp4a_kernel(const int32_t *__restrict__ A, const int32_t *__restrict__ W, i
 
 }  // namespace
 
-cudaError_t launch_xeng_dp4a(const int32_t *A, const int32_t *W, int n, int n_pad, int fc,
-                             int tw_pad, int32_t *acc, int f0, bool fresh, cudaStream_t s)
+template <int T>
+cudaError_t launch_tile(const int32_t *A, const int32_t *W, int n, int n_pad, int fc, int tw_pad,
+                        int32_t *acc, int f0, bool fresh, cudaStream_t s)
 {
-    if (fc <= 0) return cudaSuccess;
     const int nb = n_pad / T;
     dim3 grid(nb * (nb + 1) / 2, fc);
     if (fresh)
-        xeng_dp4a_kernel<true><<<grid, kThreads, 0, s>>>(A, W, n, n_pad, tw_pad, acc, f0);
+        xeng_dp4a_kernel<T, true><<<grid, threads_for<T>(), 0, s>>>(A, W, n, n_pad, tw_pad, acc, f0);
     else
-        xeng_dp4a_kernel<false><<<grid, kThreads, 0, s>>>(A, W, n, n_pad, tw_pad, acc, f0);
+        xeng_dp4a_kernel<T, false><<<grid, threads_for<T>(), 0, s>>>(A, W, n, n_pad, tw_pad, acc, f0);
     return cudaGetLastError();
+}
+
+cudaError_t launch_xeng_dp4a(const int32_t *A, const int32_t *W, int n, int n_pad, int fc,
+                             int tw_pad, int32_t *acc, int f0, bool fresh, int tile, cudaStream_t s)
+{
+    if (fc <= 0) return cudaSuccess;
+    if (n_pad % tile != 0) return cudaErrorInvalidValue;
+    if (tile == 32) return launch_tile<32>(A, W, n, n_pad, fc, tw_pad, acc, f0, fresh, s);
+    if (tile == 64) return launch_tile<64>(A, W, n, n_pad, fc, tw_pad, acc, f0, fresh, s);
+    return cudaErrorInvalidValue;
 }
 
 }  // namespace corr

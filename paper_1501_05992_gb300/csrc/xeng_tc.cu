@@ -52,6 +52,7 @@ namespace corr {
 namespace {
 
 constexpr int kTile = 128;                    // inputs per tile side
+constexpr int kMaxArrays = kTcMaxArrays;      // arrays correlated by one launch
 constexpr int kTc = 64;                       // samples per pipeline stage
 constexpr int kPackedStages = 6;
 constexpr int kPrefetchStages = 12;           // L2 prefetch distance of the packed loads
@@ -83,11 +84,24 @@ constexpr int kSmemBytes = kSmMisc + 64 + 1024;                                 
 constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | (1u << 15) | (1u << 16) |
                             ((256u >> 3) << 17) | ((128u >> 4) << 24);
 
-struct Params {
-    int n, n_chan, nt, n_tiles, n_items, n_stages;
-    int zero_invalid, fresh;
+// One array of a launch.  Items (channel, I tile, J tile) of array a are
+// numbered item_begin .. item_begin + n_chan * per_chan - 1; the host orders
+// the arrays by decreasing n_stages so that a CTA's last items are its
+// shortest (a static longest-first schedule).
+struct ArrayParams {
     int32_t *acc;
+    int n, n_chan, nt, n_tiles, per_chan, n_stages, item_begin;
+    int zero_invalid, fresh;
+};
+
+struct Params {
+    ArrayParams a[kMaxArrays];
+    int n_arrays, n_items;
     DeviceStatus *status;
+};
+
+struct Tmaps {
+    CUtensorMap m[kMaxArrays];
 };
 
 // ------------------------------------------------------------ PTX helpers --
@@ -256,6 +270,24 @@ __device__ __forceinline__ void item_tiles(int p, int &I, int &J)
     J = p - i * (i + 1) / 2;
 }
 
+struct Item {
+    int a, f, I, J;
+    bool diag;
+};
+
+__device__ __forceinline__ Item decode_item(const Params &p, int item)
+{
+    Item it;
+    it.a = 0;
+    while (it.a + 1 < p.n_arrays && item >= p.a[it.a + 1].item_begin) ++it.a;
+    const ArrayParams &A = p.a[it.a];
+    const int local = item - A.item_begin;
+    it.f = local / A.per_chan;
+    item_tiles(local - it.f * A.per_chan, it.I, it.J);
+    it.diag = it.I == it.J;
+    return it;
+}
+
 // 4 packed bytes (r << 4 | m) -> E4M3 codes u = nibble ^ 8 (value u * 2^-9).
 __device__ __forceinline__ void codes(uint32_t w, bool zero_invalid, uint32_t &R, uint32_t &M)
 {
@@ -273,7 +305,7 @@ __device__ __forceinline__ void codes(uint32_t w, bool zero_invalid, uint32_t &R
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
+xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Params p)
 {
     extern __shared__ uint8_t smem_raw[];
     uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -313,7 +345,8 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
         mbar_init(bar_drain, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-        asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmap)) : "memory");
+        for (int a = 0; a < p.n_arrays; ++a)
+            asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmaps.m[a])) : "memory");
     }
     for (int e = threadIdx.x; e < kSumsBytes / 4; e += kThreads) sums[e] = 0;
     if (warp == 1) {
@@ -334,20 +367,20 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
             uint32_t phase = 0;
             uint32_t issued = 0, issued_phase = 0;   // per slot: a load was issued / its parity
             bool ok = true;
-            const int per_chan = (p.n_tiles * (p.n_tiles + 1)) / 2;
             for (int item = first_item; ok && item < p.n_items; item += item_step) {
-                const int f = item / per_chan;
-                int I, J;
-                item_tiles(item % per_chan, I, J);
-                const bool diag = I == J;
-                for (int s = 0; s < kPrefetchStages && s < p.n_stages; ++s) {
-                    tma_prefetch_3d(&tmap, J * kTile, f, s * kTc);
-                    if (!diag) tma_prefetch_3d(&tmap, I * kTile, f, s * kTc);
+                const Item it = decode_item(p, item);
+                const ArrayParams &A = p.a[it.a];
+                const CUtensorMap *tmap = &tmaps.m[it.a];
+                const int f = it.f, I = it.I, J = it.J;
+                const bool diag = it.diag;
+                for (int s = 0; s < kPrefetchStages && s < A.n_stages; ++s) {
+                    tma_prefetch_3d(tmap, J * kTile, f, s * kTc);
+                    if (!diag) tma_prefetch_3d(tmap, I * kTile, f, s * kTc);
                 }
-                for (int s = 0; s < p.n_stages; ++s) {
-                    if (s + kPrefetchStages < p.n_stages) {
-                        tma_prefetch_3d(&tmap, J * kTile, f, (s + kPrefetchStages) * kTc);
-                        if (!diag) tma_prefetch_3d(&tmap, I * kTile, f, (s + kPrefetchStages) * kTc);
+                for (int s = 0; s < A.n_stages; ++s) {
+                    if (s + kPrefetchStages < A.n_stages) {
+                        tma_prefetch_3d(tmap, J * kTile, f, (s + kPrefetchStages) * kTc);
+                        if (!diag) tma_prefetch_3d(tmap, I * kTile, f, (s + kPrefetchStages) * kTc);
                     }
                     if (!mbar_wait(bar_packed_empty(stage), phase ^ 1u, abort, p.status, 1)) {
                         ok = false;
@@ -356,8 +389,8 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                     const uint32_t full = bar_packed_full(stage);
                     const uint32_t dst = sbase + kSmPacked + stage * kPackedStageBytes;
                     mbar_expect_tx(full, diag ? kPackedTileBytes : 2 * kPackedTileBytes);
-                    tma_load_3d(dst + kPackedTileBytes, &tmap, full, J * kTile, f, s * kTc);
-                    if (!diag) tma_load_3d(dst, &tmap, full, I * kTile, f, s * kTc);
+                    tma_load_3d(dst + kPackedTileBytes, tmap, full, J * kTile, f, s * kTc);
+                    if (!diag) tma_load_3d(dst, tmap, full, I * kTile, f, s * kTc);
                     issued |= 1u << stage;
                     issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
                     if (++stage == kPackedStages) {
@@ -383,9 +416,9 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
             int local = 0;
             bool ok = true;
             for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
-                int I, J;
-                item_tiles(item % ((p.n_tiles * (p.n_tiles + 1)) / 2), I, J);
-                const bool diag = I == J;
+                const Item it = decode_item(p, item);
+                const int n_stages = p.a[it.a].n_stages;
+                const bool diag = it.diag;
                 const int buf = local & 1;
                 if (!mbar_wait(bar_acc_empty(buf), ((acc_phase >> buf) & 1u) ^ 1u, abort, p.status, 2)) {
                     ok = false;
@@ -395,7 +428,7 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                 fence_after();
                 const uint32_t d_tmem = tmem + uint32_t(buf * 256);
                 uint32_t accum = 0;
-                for (int s = 0; s < p.n_stages; ++s) {
+                for (int s = 0; s < n_stages; ++s) {
                     if (!mbar_wait(bar_plane_full(stage), phase, abort, p.status, 3)) {
                         ok = false;
                         break;
@@ -434,7 +467,6 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
         // stage, for both tiles, so its per-input sums never leave registers
         const int ct = threadIdx.x - kFirstConvWarp * 32;        // 0..511
         const int c = ct & 7, row = ct >> 3;                      // chunk column, row 0..63
-        const bool zi = p.zero_invalid != 0;
         const uint32_t so = uint32_t(row * 128 + ((c ^ (row & 7)) << 4));   // swizzled plane offset
         const uint32_t po = uint32_t(row * 128 + c * 16);                   // packed offset
         int pstage = 0, cstage = 0;
@@ -442,9 +474,10 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
         int local = 0;
         bool ok = true;
         for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
-            int I, J;
-            item_tiles(item % ((p.n_tiles * (p.n_tiles + 1)) / 2), I, J);
-            const bool diag = I == J;
+            const Item it = decode_item(p, item);
+            const int n_stages = p.a[it.a].n_stages;
+            const bool zi = p.a[it.a].zero_invalid != 0;
+            const bool diag = it.diag;
             // per-input code sums: byte lanes (<= 16 rows), then 16-bit lanes
             uint32_t b8[2][2][4], s16lo[2][2][4], s16hi[2][2][4];
 #pragma unroll
@@ -453,7 +486,7 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                 for (int q = 0; q < 2; ++q)
 #pragma unroll
                     for (int k = 0; k < 4; ++k) b8[t][q][k] = s16lo[t][q][k] = s16hi[t][q][k] = 0;
-            for (int s = 0; s < p.n_stages; ++s) {
+            for (int s = 0; s < n_stages; ++s) {
                 if (!mbar_wait(bar_packed_full(pstage), pphase, abort, p.status, 4) ||
                     !mbar_wait(bar_plane_empty(cstage), cphase ^ 1u, abort, p.status, 5)) {
                     ok = false;
@@ -506,7 +539,7 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                     cphase ^= 1u;
                 }
                 // byte lanes hold at most 16 rows of codes <= 15 (240): widen every 16 stages
-                if ((s & 15) == 15 || s + 1 == p.n_stages) {
+                if ((s & 15) == 15 || s + 1 == n_stages) {
 #pragma unroll
                     for (int t = 0; t < 2; ++t)
 #pragma unroll
@@ -568,14 +601,13 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
         uint32_t aphase = 0;                          // bit b: phase of buffer b
         int local = 0;
         bool ok = true;
-        const long long P = n_pairs(p.n);
-        const int T_eff = p.n_stages * kTc;
-        const int per_chan = (p.n_tiles * (p.n_tiles + 1)) / 2;
         for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
-            const int f = item / per_chan;
-            int I, J;
-            item_tiles(item % per_chan, I, J);
-            const bool diag = I == J;
+            const Item it = decode_item(p, item);
+            const ArrayParams &A = p.a[it.a];
+            const long long P = n_pairs(A.n);
+            const int T_eff = A.n_stages * kTc;
+            const int f = it.f, I = it.I, J = it.J;
+            const bool diag = it.diag;
             const int buf = local & 1;
             // the four epilogue warps decide together whether to go on, so that
             // none of them is ever left waiting at a named barrier
@@ -597,7 +629,7 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
             const int Sri = si[sum_slot(il)], Smi = si[kTile + sum_slot(il)];
             const int Ei = Sri + Smi, Di = Smi - Sri;
             const int base_re = 128 * T_eff - 8 * Ei;
-            int32_t *out = p.acc + ((size_t)f * P + (size_t)i * (i + 1) / 2) * 2;
+            int32_t *out = A.acc + ((size_t)f * P + (size_t)i * (i + 1) / 2) * 2;
             const uint32_t taddr = tmem + uint32_t(buf * 256) + (uint32_t(q * 32) << 16);
 #pragma unroll 1
             for (int c0 = 0; c0 < kTile; c0 += 16) {
@@ -605,7 +637,7 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                 tmem_ld16(taddr + c0, vre);
                 tmem_ld16(taddr + 128 + c0, vim);
                 tmem_wait_ld();
-                if (i < p.n) {
+                if (i < A.n) {
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
                         const int jl = c0 + k;
@@ -617,7 +649,7 @@ xeng_tc_kernel(const __grid_constant__ CUtensorMap tmap, Params p)
                         const int re = pre + base_re - 8 * (Srj + Smj);
                         const int im = pim - 8 * Di + 8 * (Smj - Srj);
                         int2 *dst = reinterpret_cast<int2 *>(out + size_t(j) * 2);
-                        if (p.fresh) {
+                        if (A.fresh) {
                             *dst = make_int2(re, im);
                         } else {
                             int2 v = *dst;
@@ -689,12 +721,9 @@ bool tc_supported(int n_inputs, int device)
     return cached[device] == 1;
 }
 
-cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool zero_invalid,
-                           int32_t *acc, bool fresh, DeviceStatus *status, cudaStream_t s)
+cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus *status, cudaStream_t s)
 {
-    if (nt <= 0) return cudaSuccess;
-    if (nt > kTcMaxSamples || n % 16 != 0 || (reinterpret_cast<uintptr_t>(volt) & 15) != 0)
-        return cudaErrorInvalidValue;
+    if (count < 0 || count > kMaxArrays) return cudaErrorInvalidValue;
     auto enc = encoder();
     if (!enc) return cudaErrorNotSupported;
     int dev = 0;
@@ -711,29 +740,63 @@ cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool 
             g_attr_set[dev] = 1;
         }
     }
-    CUtensorMap map;
-    const cuuint64_t dims[3] = {cuuint64_t(n), cuuint64_t(n_chan), cuuint64_t(nt)};
-    const cuuint64_t strides[2] = {cuuint64_t(n), cuuint64_t(n) * cuuint64_t(n_chan)};
-    const cuuint32_t box[3] = {cuuint32_t(kTile), 1u, cuuint32_t(kTc)};
-    const cuuint32_t estr[3] = {1u, 1u, 1u};
-    CUresult cr = enc(&map, CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(volt), dims, strides, box,
-                      estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
-                      CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-    if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+    // arrays with work, longest items first
+    int order[kMaxArrays], m = 0;
+    for (int k = 0; k < count; ++k) {
+        const TcArray &A = arrays[k];
+        if (A.nt <= 0) continue;
+        if (A.nt > kTcMaxSamples || A.n < 16 || A.n % 16 != 0 || A.n_chan < 1 || !A.acc ||
+            (reinterpret_cast<uintptr_t>(A.volt) & 15) != 0)
+            return cudaErrorInvalidValue;
+        order[m++] = k;
+    }
+    if (m == 0) return cudaSuccess;
+    for (int x = 1; x < m; ++x)
+        for (int y = x; y > 0 && arrays[order[y]].nt > arrays[order[y - 1]].nt; --y) {
+            const int t = order[y];
+            order[y] = order[y - 1];
+            order[y - 1] = t;
+        }
+    Tmaps maps;
     Params prm{};
-    prm.n = n;
-    prm.n_chan = n_chan;
-    prm.nt = nt;
-    prm.n_tiles = (n + kTile - 1) / kTile;
-    prm.n_items = n_chan * (prm.n_tiles * (prm.n_tiles + 1) / 2);
-    prm.n_stages = (nt + kTc - 1) / kTc;
-    prm.zero_invalid = zero_invalid ? 1 : 0;
-    prm.fresh = fresh ? 1 : 0;
-    prm.acc = acc;
+    long long items = 0;
+    for (int k = 0; k < m; ++k) {
+        const TcArray &A = arrays[order[k]];
+        const cuuint64_t dims[3] = {cuuint64_t(A.n), cuuint64_t(A.n_chan), cuuint64_t(A.nt)};
+        const cuuint64_t strides[2] = {cuuint64_t(A.n), cuuint64_t(A.n) * cuuint64_t(A.n_chan)};
+        const cuuint32_t box[3] = {cuuint32_t(kTile), 1u, cuuint32_t(kTc)};
+        const cuuint32_t estr[3] = {1u, 1u, 1u};
+        CUresult cr = enc(&maps.m[k], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(A.volt), dims,
+                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+                          CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+        if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
+        ArrayParams &P = prm.a[k];
+        P.acc = A.acc;
+        P.n = A.n;
+        P.n_chan = A.n_chan;
+        P.nt = A.nt;
+        P.n_tiles = (A.n + kTile - 1) / kTile;
+        P.per_chan = P.n_tiles * (P.n_tiles + 1) / 2;
+        P.n_stages = (A.nt + kTc - 1) / kTc;
+        P.item_begin = int(items);
+        P.zero_invalid = A.zero_invalid ? 1 : 0;
+        P.fresh = A.fresh ? 1 : 0;
+        items += (long long)A.n_chan * P.per_chan;
+    }
+    if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
+    prm.n_arrays = m;
+    prm.n_items = int(items);
     prm.status = status;
     const int grid = prm.n_items < g_sm_count[dev] ? prm.n_items : g_sm_count[dev];
-    xeng_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(map, prm);
+    xeng_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, prm);
     return cudaGetLastError();
+}
+
+cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool zero_invalid,
+                           int32_t *acc, bool fresh, DeviceStatus *status, cudaStream_t s)
+{
+    const TcArray a{volt, acc, n_chan, n, nt, zero_invalid, fresh};
+    return launch_xeng_tc_batch(&a, 1, status, s);
 }
 
 }  // namespace corr

@@ -1,0 +1,146 @@
+"""Batched arrays (one persistent tensor-core launch), CUDA-graph replay,
+CUDA-core tile shapes and the autotuner, all bit-exact against the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1501_05992_gb300 import autotune, corr
+
+from _gpu import path_available
+
+pytestmark = pytest.mark.gpu
+
+
+def _rand(shape, seed):
+    return np.random.default_rng(seed).integers(0, 256, shape, dtype=np.uint8)
+
+
+def _check_batch(specs, volts_np, chunks=1):
+    b = corr.Batch(specs)
+    vt = [torch.from_numpy(v).cuda() for v in volts_np]
+    T = [v.shape[0] for v in volts_np]
+    for k in range(chunks):
+        part = [v[(t * k) // chunks:(t * (k + 1)) // chunks].contiguous() for v, t in zip(vt, T)]
+        b.accumulate(part)
+    outs = b.dump()
+    b.sync()
+    for a, (v, o) in enumerate(zip(volts_np, outs)):
+        assert np.array_equal(o.cpu().numpy(), oracle.to_int32(oracle.xmac(v))), f"array {a}"
+    return b
+
+
+def test_uneven_arrays_in_one_launch():
+    """Three arrays shaped like the uneven-batch workload (fewer channels)."""
+    if not path_available("tc_fp8", 128):
+        pytest.skip("tc_fp8 unsupported")
+    specs = [{"n_inputs": 128, "n_chan": 40, "n_time_per_int": 2000, "path": "tc_fp8"},
+             {"n_inputs": 256, "n_chan": 24, "n_time_per_int": 700, "path": "tc_fp8"},
+             {"n_inputs": 1024, "n_chan": 3, "n_time_per_int": 300, "path": "tc_fp8"}]
+    volts = [_rand((2000, 40, 128), 1), _rand((700, 24, 256), 2), _rand((300, 3, 1024), 3)]
+    b = _check_batch(specs, volts)
+    assert b.paths == ["tc_fp8"] * 3
+    _check_batch(specs, volts, chunks=3)
+
+
+def test_more_arrays_than_one_launch_holds():
+    if not path_available("tc_fp8", 64):
+        pytest.skip("tc_fp8 unsupported")
+    shapes = [(64, 5, 130), (128, 3, 64), (192, 2, 200), (64, 7, 1), (256, 1, 90), (48, 4, 333)]
+    specs = [{"n_inputs": n, "n_chan": f, "n_time_per_int": t, "path": "tc_fp8"} for n, f, t in shapes]
+    volts = [_rand((t, f, n), 10 + k) for k, (n, f, t) in enumerate(shapes)]
+    _check_batch(specs, volts)
+
+
+def test_mixed_paths_and_skipped_arrays():
+    specs = [{"n_inputs": 64, "n_chan": 6, "n_time_per_int": 500, "path": "cudacore", "tile": 32},
+             {"n_inputs": 128, "n_chan": 4, "n_time_per_int": 500, "path": "auto"},
+             {"n_inputs": 40, "n_chan": 5, "n_time_per_int": 500, "path": "mma_i8"}]
+    volts = [_rand((500, 6, 64), 21), _rand((500, 4, 128), 22), _rand((500, 5, 40), 23)]
+    _check_batch(specs, volts)
+    b = corr.Batch(specs)
+    b.accumulate([torch.from_numpy(volts[0]).cuda(), None, None])
+    assert [b.samples(a) for a in range(3)] == [500, 0, 0]
+    outs = b.dump([torch.empty((6, 64 * 65 // 2, 2), dtype=torch.int32, device="cuda"), None, None])
+    b.sync()
+    assert np.array_equal(outs[0].cpu().numpy(), oracle.to_int32(oracle.xmac(volts[0])))
+
+
+def test_long_batched_integration_splits_launches():
+    if not path_available("tc_fp8", 128):
+        pytest.skip("tc_fp8 unsupported")
+    specs = [{"n_inputs": 128, "n_chan": 2, "n_time_per_int": 40000, "path": "tc_fp8"},
+             {"n_inputs": 256, "n_chan": 1, "n_time_per_int": 33000, "path": "tc_fp8"}]
+    volts = [np.full((40000, 2, 128), 0x77, np.uint8), _rand((33000, 1, 256), 31)]
+    _check_batch(specs, volts)
+
+
+def test_overflow_in_one_array_enqueues_nothing():
+    specs = [(64, 2, 100), (128, 2, 50)]
+    b = corr.Batch(specs)
+    v0 = torch.zeros((80, 2, 64), dtype=torch.uint8, device="cuda")
+    v1 = torch.zeros((60, 2, 128), dtype=torch.uint8, device="cuda")
+    with pytest.raises(corr.CorrError) as e:
+        b.accumulate([v0, v1])
+    assert e.value.status == corr.CORR_E_OVERFLOW
+    assert b.samples(0) == 0 and b.samples(1) == 0
+    b.accumulate([v0, v1[:50].contiguous()])
+    assert b.samples(0) == 80 and b.samples(1) == 50
+    b.dump()
+    b.sync()
+
+
+def test_graph_replays_whole_integrations():
+    specs = [{"n_inputs": 128, "n_chan": 8, "n_time_per_int": 1000},
+             {"n_inputs": 64, "n_chan": 3, "n_time_per_int": 1000, "path": "cudacore"}]
+    volts = [_rand((1000, 8, 128), 41), _rand((1000, 3, 64), 42)]
+    b = corr.Batch(specs)
+    vt = [torch.from_numpy(v).cuda() for v in volts]
+    stream = torch.cuda.Stream()
+    graph, outs = b.capture(vt, stream=stream)
+    assert b.samples(0) == 0 and b.samples(1) == 0
+    want = [oracle.to_int32(oracle.xmac(v)) for v in volts]
+    for rep in range(3):
+        for o in outs:
+            o.fill_(-7)
+        torch.cuda.synchronize()
+        graph.launch(stream)
+        stream.synchronize()
+        for a in range(2):
+            assert np.array_equal(outs[a].cpu().numpy(), want[a]), (rep, a)
+    # new data in the captured input buffers is picked up by the next replay
+    new0 = _rand((1000, 8, 128), 43)
+    vt[0].copy_(torch.from_numpy(new0))
+    torch.cuda.synchronize()
+    graph.launch(stream)
+    stream.synchronize()
+    assert np.array_equal(outs[0].cpu().numpy(), oracle.to_int32(oracle.xmac(new0)))
+    b.sync(stream)
+    graph.close()
+
+
+@pytest.mark.parametrize("tile", [32, 64])
+@pytest.mark.parametrize("shape", [(1, 1, 5), (17, 3, 65), (33, 2, 129), (100, 2, 64)])
+def test_cudacore_tiles_exact(tile, shape):
+    N, F, T = shape
+    volt = _rand((T, F, N), N + F + T + tile)
+    c = corr.Correlator(N, F, T, path="cudacore")
+    c.set_tile(tile)
+    c.accumulate(torch.from_numpy(volt).cuda())
+    got = c.dump().cpu().numpy()
+    c.sync()
+    c.close()
+    assert np.array_equal(got, oracle.to_int32(oracle.xmac(volt)))
+
+
+def test_autotune_picks_and_caches(tmp_path):
+    cache = str(tmp_path / "tune.json")
+    r = autotune.tune(256, 8, 500, cache_path=cache, reps=1)
+    assert r["path"] in ("tc_fp8", "mma_i8", "cudacore") and r["ms"]
+    again = autotune.tune(256, 8, 500, cache_path=cache, reps=1)
+    assert again == r
+    small = autotune.tune(16, 8, 500, cache_path=cache, reps=1)
+    plan = autotune.plan([(256, 8, 500), (16, 8, 500)], cache_path=cache)
+    assert plan[0]["path"] == r["path"] and plan[1]["path"] == small["path"]
+    volts = [_rand((500, 8, 256), 51), _rand((500, 8, 16), 52)]
+    _check_batch(plan, volts)
