@@ -33,9 +33,10 @@ UNIT = "CMAC/s"
 SAMPLE_RATE_HZ = 1.0e4            # 10 kHz fine channels: one sample per channel per 100 us
 
 WORKLOADS = {
-    # name: (n_inputs, n_chan, samples per integration, integrations, recipe seed)
-    "full_band": (256, 3072, 5000, 16, 1503),
-    "coarse_channel": (256, 128, 5000, 1, 1502),
+    # name: arrays [(n_inputs, n_chan, samples per integration)], integrations per step, seed
+    "full_band": ([(256, 3072, 5000)], 16, 1503),
+    "coarse_channel": ([(256, 128, 5000)], 1, 1502),
+    "uneven_batch": ([(128, 1536, 2000), (256, 3072, 5000), (1024, 512, 10000)], 1, 1504),
 }
 
 
@@ -47,6 +48,10 @@ def parse_args():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", default="auto", choices=["auto", "cudacore", "mma_i8", "tc_fp8"])
     ap.add_argument("--workload", default="full_band", choices=sorted(WORKLOADS))
+    ap.add_argument("--mode", default="graph", choices=["graph", "direct"],
+                    help="graph: one captured CUDA graph per integration; direct: C-ABI calls")
+    ap.add_argument("--autotune", action="store_true",
+                    help="pick path and tile per array by measurement (cached)")
     ap.add_argument("--e2e-steps", type=int, default=2)
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
@@ -172,10 +177,11 @@ def host_sample_slab(n_inputs, n_chan, n_time, seed, channels):
 def run_reference(args, world, rank):
     if rank != 0:
         return
-    n_inputs, n_chan, t_int, n_int, seed = WORKLOADS[args.workload]
-    P = n_inputs * (n_inputs + 1) // 2
+    arrays, n_int, seed = WORKLOADS[args.workload]
     import oracle
     oracle.build()
+    n_inputs, n_chan, t_int = arrays[0]
+    P = n_inputs * (n_inputs + 1) // 2
     slab = host_sample_slab(n_inputs, n_chan, t_int, seed, channels=min(n_chan, 64))
     budget = max(1.0, 150.0 / max(1, args.steps + args.warmup))
     for _ in range(args.warmup):
@@ -186,14 +192,15 @@ def run_reference(args, world, rank):
         rates.append(r)
         descs.append(d)
     value = statistics.median(rates)
-    step_cmac = P * n_chan * t_int * n_int
+    step_cmac = sum(n * (n + 1) // 2 * f * t for n, f, t in arrays) * n_int
+    rt_rate = sum(n * (n + 1) // 2 * f for n, f, t in arrays) * SAMPLE_RATE_HZ
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_cmac / value * 1e3, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-        "x_real_time": value / (P * n_chan * SAMPLE_RATE_HZ),
-        "config": workload_config(args, "oracle (CPU, int64 triple loop)"),
+        "x_real_time": value / rt_rate,
+        "config": workload_config(args, ["oracle (CPU, int64 triple loop)"]),
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                          "sample": descs[-1]},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
@@ -201,14 +208,16 @@ def run_reference(args, world, rank):
     print(json.dumps(line), flush=True)
 
 
-def workload_config(args, path):
-    n_inputs, n_chan, t_int, n_int, seed = WORKLOADS[args.workload]
-    return {"workload": f"{args.workload}: {n_inputs} inputs x {n_chan} ch x {n_int} integrations "
-                        f"x {t_int} samples (4+4-bit, gauss3 recipe, seed {seed})",
-            "n_inputs": n_inputs, "n_chan": n_chan, "samples_per_integration": t_int,
-            "integrations_per_step": n_int, "path": path,
-            "l2": "no flush: each step reads %.1f GB of voltages (> 129 MB L2)"
-                  % (n_inputs * n_chan * t_int * n_int / 1e9),
+def workload_config(args, paths):
+    arrays, n_int, seed = WORKLOADS[args.workload]
+    desc = " + ".join(f"{n} inputs x {f} ch x {t} samples" for n, f, t in arrays)
+    gb = sum(n * f * t for n, f, t in arrays) * n_int / 1e9
+    return {"workload": f"{args.workload}: {desc}, {n_int} integration(s) per step "
+                        f"(4+4-bit, gauss3 recipe, seed {seed})",
+            "arrays": [{"n_inputs": n, "n_chan": f, "samples_per_integration": t, "path": p}
+                       for (n, f, t), p in zip(arrays, paths)],
+            "integrations_per_step": n_int, "mode": args.mode,
+            "l2": "no flush: each step reads %.1f GB of voltages (> 129 MB L2)" % gb,
             "parallelism": "replicas (channels shard with no exchange)"}
 
 
@@ -248,37 +257,75 @@ def roofline_for(path, ops_per_launch, avg_ms, peaks, src, sm_count):
 
 def run_ours(args, world, rank, local):
     import torch
-    from paper_1501_05992_gb300 import corr
+    from paper_1501_05992_gb300 import autotune, corr
     from synth import voltgen as vg
     from synth.gpu import DeviceGenerator
 
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
-    n_inputs, n_chan, t_int, n_int, seed = WORKLOADS[args.workload]
-    P = n_inputs * (n_inputs + 1) // 2
-    T_total = t_int * n_int
-    # every rank correlates its own array (weak scaling, no exchange)
-    params = vg.gauss3_params(seed, n_inputs, n_chan, array=rank)
-    gen = DeviceGenerator(params, dev)
-    volt = torch.empty((T_total, n_chan, n_inputs), dtype=torch.uint8, device=dev)
-    for k in range(n_int):
-        gen.fill(volt[k * t_int:(k + 1) * t_int], t0=k * t_int)
-    outs = [torch.empty((n_chan, P, 2), dtype=torch.int32, device=dev) for _ in range(2)]
-    c = corr.Correlator(n_inputs, n_chan, t_int, path=args.path, device=dev)
-    path = c.path
-    stream = torch.cuda.current_stream(dev)
-
-    def step():
+    arrays, n_int, seed = WORKLOADS[args.workload]
+    # every rank correlates its own arrays (weak scaling, no exchange)
+    volts = []
+    for a, (n, f, t) in enumerate(arrays):
+        gen = DeviceGenerator(vg.gauss3_params(seed, n, f, array=a + 8 * rank), dev)
+        v = torch.empty((t * n_int, f, n), dtype=torch.uint8, device=dev)
         for k in range(n_int):
-            c.accumulate(volt[k * t_int:(k + 1) * t_int])
-            c.dump(outs[k & 1])
+            gen.fill(v[k * t:(k + 1) * t], t0=k * t)
+        volts.append(v)
+    specs = [{"n_inputs": n, "n_chan": f, "n_time_per_int": t, "path": args.path}
+             for n, f, t in arrays]
+    tuned = None
+    if args.autotune:
+        cache = os.path.join(ROOT, "gpurun_out", "autotune_cache.json") \
+            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
+        specs = autotune.plan(specs, cache_path=cache)
+        tuned = [{k: s[k] for k in ("path", "tile")} for s in specs]
+    batch = corr.Batch(specs, device=dev)
+    paths = batch.paths
+    stream = torch.cuda.Stream(dev)
+    outs = [batch._outs(None) for _ in range(2)]
+    step_cmac = sum(n * (n + 1) // 2 * f * t for n, f, t in arrays) * n_int
+    rt_rate = sum(n * (n + 1) // 2 * f for n, f, t in arrays) * SAMPLE_RATE_HZ
 
-    for _ in range(args.warmup):
-        step()
-    c.sync()
-    torch.cuda.synchronize(dev)
-    c.profile_read(reset=True)
-    c.profile_enable(True)
+    def integration(k):
+        return [v[k * t:(k + 1) * t] for v, (n, f, t) in zip(volts, arrays)]
+
+    # kernel timing: the library profiler brackets every X-engine and dump
+    # launch with CUDA events on the launch stream (direct mode); in graph mode
+    # the bench brackets every graph launch (= X-engine + dump of one
+    # integration) with its own events on the same stream, and the dump's
+    # share comes from a short profiled direct pass after the timed region
+    graphs = []
+    if args.mode == "graph":
+        for k in range(n_int):
+            g, _ = batch.capture(integration(k), outs[k & 1], stream=stream)
+            graphs.append(g)
+        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(n_int)]
+        graph_ms = []
+
+        def step(timed=False):
+            for k, g in enumerate(graphs):
+                if timed:
+                    gev[k][0].record(stream)
+                g.launch(stream)
+                if timed:
+                    gev[k][1].record(stream)
+            if timed:
+                graph_ms.append(gev)
+    else:
+        def step(timed=False):
+            for k in range(n_int):
+                batch.accumulate(integration(k), stream=stream)
+                batch.dump(outs[k & 1], stream=stream)
+
+    with torch.cuda.stream(stream):
+        for _ in range(args.warmup):
+            step()
+    stream.synchronize()
+    batch.profile_read(reset=True)
+    if args.mode == "direct":
+        batch.profile_enable(True)
     clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     barrier(world)
     torch.cuda.synchronize(dev)
@@ -286,65 +333,98 @@ def run_ours(args, world, rank, local):
         clocks.start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
-    for _ in range(args.steps):
-        step()
+    for st in range(args.steps):
+        # per-graph events on the last step only (they are reused)
+        step(timed=(args.mode == "graph" and st == args.steps - 1))
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(world)
     clk = clocks.stop() if clocks else None
-    c.profile_enable(False)
-    prof = c.profile_read(reset=True)
-    c.sync()
+    batch.sync(stream)
     elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
-    step_cmac = P * n_chan * T_total
     value = step_cmac * args.steps * world / (elapsed_ms * 1e-3)
-    launches = sum(v["launches"] for v in prof.values())
 
-    xe = prof["xengine"]
+    if args.mode == "direct":
+        prof = batch.profile_read(reset=True)
+        batch.profile_enable(False)
+        launches_per_step = sum(p[k]["launches"] for p in prof for k in p) // max(1, args.steps)
+        xe_ms = sum(p["xengine"]["ms"] for p in prof)
+        xe_timed = sum(p["xengine"]["timed"] for p in prof)
+        kernel_ms = {k: sum(p[k]["ms"] for p in prof) / args.steps for k in prof[0]}
+        timing_note = "library CUDA events around every X-engine launch in the timed region"
+    else:
+        # dump share from one profiled direct integration after the timed region
+        batch.profile_enable(True)
+        with torch.cuda.stream(stream):
+            batch.accumulate(integration(0), stream=stream)
+            batch.dump(outs[0], stream=stream)
+        stream.synchronize()
+        prof = batch.profile_read(reset=True)
+        batch.profile_enable(False)
+        per_int_launches = sum(p[k]["launches"] for p in prof for k in p)
+        launches_per_step = per_int_launches * n_int
+        dump_ms = sum(p["dump"]["ms"] for p in prof)
+        g_ms = [a.elapsed_time(b) for a, b in gev]
+        xe_ms = sum(max(0.0, m - dump_ms) for m in g_ms)
+        xe_timed = len(g_ms) * max(1, sum(p["xengine"]["launches"] for p in prof))
+        kernel_ms = {"graph_per_integration": sum(g_ms) / len(g_ms), "dump": dump_ms,
+                     "xengine_per_integration": xe_ms / len(g_ms)}
+        timing_note = ("CUDA events around every graph launch of the last timed step, "
+                       "minus the dump time of a profiled direct integration")
+    xe_per_step = xe_timed if args.mode == "graph" else xe_timed // max(1, args.steps)
     peaks, src = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
-    ops_total = 8.0 * step_cmac * args.steps
-    roof = roofline_for(path, ops_total / max(1, xe["timed"]), xe["ms"] / max(1, xe["timed"]),
-                        peaks, src, sm_count)
+    ops_per_launch = 8.0 * step_cmac / max(1, xe_per_step)
+    avg_ms = xe_ms / max(1, xe_timed)
+    main_path = paths[max(range(len(arrays)), key=lambda a: arrays[a][0] ** 2 * arrays[a][1] * arrays[a][2])]
+    roof = roofline_for(main_path, ops_per_launch, avg_ms, peaks, src, sm_count)
     roof["traffic"] = None
     roof["kernel"] = {"cudacore": "xeng_dp4a_kernel", "mma_i8": "xeng_mma8_kernel",
-                      "tc_fp8": "xeng_tc_kernel"}[path]
-    roof["launches"] = xe["timed"]
-    roof["avg_launch_ms"] = xe["ms"] / max(1, xe["timed"])
+                      "tc_fp8": "xeng_tc_kernel"}[main_path]
+    roof["launches_per_step"] = xe_per_step
+    roof["avg_launch_ms"] = avg_ms
+    roof["timing"] = timing_note
 
     # ---- end to end through the host-buffer C-ABI calls -------------------
     e2e = None
     if args.e2e_steps > 0:
-        h_volt = volt[:t_int].cpu().pin_memory()          # one integration, reused
-        h_outs = [torch.empty((n_chan, P, 2), dtype=torch.int32).pin_memory() for _ in range(2)]
+        ctxs = [corr.Correlator(n, f, t, path=p, device=dev) for (n, f, t), p in zip(arrays, paths)]
+        h_volts = [v[:t].cpu().pin_memory() for v, (n, f, t) in zip(volts, arrays)]
+        h_outs = [[torch.empty((f, n * (n + 1) // 2, 2), dtype=torch.int32).pin_memory()
+                   for _ in range(2)] for n, f, t in arrays]
 
         def step_host():
             for k in range(n_int):
-                c.accumulate_host(h_volt)
-                c.dump_host(h_outs[k & 1])
+                for a, c in enumerate(ctxs):
+                    c.accumulate_host(h_volts[a], stream=stream)
+                    c.dump_host(h_outs[a][k & 1], stream=stream)
 
         step_host()
-        c.sync()
+        stream.synchronize()
         barrier(world)
-        torch.cuda.synchronize(dev)
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         t0 = time.perf_counter()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
         for _ in range(args.e2e_steps):
             step_host()
         e1.record(stream)
         torch.cuda.synchronize(dev)
         wall = time.perf_counter() - t0
+        for c in ctxs:
+            c.sync(stream)
+            c.close()
         e_ms = max_over_ranks(max(e0.elapsed_time(e1), wall * 1e3), world)
         e2e = {"value": step_cmac * args.e2e_steps * world / (e_ms * 1e-3), "unit": UNIT,
-               "h2d_bytes_per_step": n_int * t_int * n_chan * n_inputs,
-               "d2h_bytes_per_step": n_int * n_chan * P * 8,
-               "note": "host voltages: one pinned integration re-sent 16 times per step"}
-        del h_volt, h_outs
+               "h2d_bytes_per_step": n_int * sum(n * f * t for n, f, t in arrays),
+               "d2h_bytes_per_step": n_int * sum(f * n * (n + 1) // 2 * 8 for n, f, t in arrays),
+               "note": "corr_accumulate_host / corr_dump_host from pinned memory; one pinned "
+                       "integration per array, re-sent for each integration of the step"}
+        del h_volts, h_outs
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        slab = volt[:t_int, :min(n_chan, 256)].cpu().numpy()
+        n, f, t = arrays[0]
+        slab = volts[0][:t, :min(f, 256)].cpu().numpy()
         rate, cores, desc = oracle_sample(slab, args.cpu_seconds)
         cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
 
@@ -354,14 +434,18 @@ def run_ours(args, world, rank, local):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"cudacore": "int8", "mma_i8": "int8", "tc_fp8": "e4m3"}[path],
-            "data": "synthetic", "x_real_time": value / (P * n_chan * SAMPLE_RATE_HZ * world),
-            "config": workload_config(args, path),
-            "gpu_launches": launches, "clocks": clk, "roofline": roof,
-            "cpu_baseline": cpu, "e2e": e2e, "kernel_ms": {k: v["ms"] for k, v in prof.items()},
+            "dtype": {"cudacore": "int8", "mma_i8": "int8", "tc_fp8": "e4m3"}[main_path],
+            "data": "synthetic", "x_real_time": value / (rt_rate * world),
+            "config": workload_config(args, paths),
+            "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roof,
+            "cpu_baseline": cpu, "e2e": e2e, "kernel_ms": kernel_ms,
         }
+        if tuned:
+            line["autotune"] = tuned
         print(json.dumps(line), flush=True)
-    c.close()
+    for g in graphs:
+        g.close()
+    batch.close()
 
 
 def main():

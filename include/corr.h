@@ -228,6 +228,10 @@ int corr_batch_path(const corr_batch *b, int a);
 /* Samples in array a's running integration. */
 long long corr_batch_samples(const corr_batch *b, int a);
 
+/* The context of array a (owned by the batch; valid until corr_batch_destroy):
+ * for corr_profile_*, corr_get_state / corr_set_state and corr_sync. */
+corr_ctx *corr_batch_array(corr_batch *b, int a);
+
 /*
  * Accumulate d_volt[a] (device, [n_time[a]][F_a][N_a]) into array a for every
  * a with d_volt[a] != NULL and n_time[a] > 0.  All checks happen before
@@ -249,6 +253,9 @@ int corr_batch_sync(corr_batch *b, void *stream);
  * integrations (every array at 0 samples, else CORR_E_STATE) and stays so:
  * each corr_graph_launch replays the full integration on the captured
  * buffers.  `stream` must not be the legacy default stream (CORR_E_ARG).
+ * Profiling events recorded during capture become graph nodes; launches that
+ * cannot be timed from them are left out of corr_profile_read's "timed" and
+ * "ms" (launch counts cover the capture only).
  */
 int corr_batch_graph_capture(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
                              int32_t *const *d_vis, void *stream, void **graph_exec);
@@ -307,7 +314,8 @@ typedef struct corr_profile {
 int corr_profile_enable(corr_ctx *ctx, int on);
 
 /* Fill *out with the counts and the summed event times since the last reset
- * (waits for the recorded events to complete); reset != 0 clears them. */
+ * (waits for the recorded events to complete; pairs that cannot be timed are
+ * not counted in timed[] and ms[]); reset != 0 clears them. */
 int corr_profile_read(corr_ctx *ctx, corr_profile *out, int reset);
 
 /* ------------------------------------------------------------------ errors -- */

@@ -112,6 +112,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_batch_bind_workspace": ([vp, vp, c_size], c_int),
             "corr_batch_path": ([vp, c_int], c_int),
             "corr_batch_samples": ([vp, c_int], ctypes.c_longlong),
+            "corr_batch_array": ([vp, c_int], vp),
             "corr_batch_accumulate": ([vp, ctypes.POINTER(vp), ctypes.POINTER(c_int), vp], c_int),
             "corr_batch_dump": ([vp, ctypes.POINTER(vp), vp], c_int),
             "corr_batch_sync": ([vp, vp], c_int),
@@ -363,6 +364,25 @@ class Batch:
 
     def samples(self, a: int) -> int:
         return int(self._lib.corr_batch_samples(self._h, a))
+
+    def _ctx(self, a: int):
+        h = self._lib.corr_batch_array(self._h, a)
+        if not h:
+            raise CorrError(self._lib.corr_last_error(), "corr_batch_array")
+        return ctypes.c_void_p(h)
+
+    def profile_enable(self, on: bool = True) -> None:
+        for a in range(len(self)):
+            _check(self._lib.corr_profile_enable(self._ctx(a), int(on)), "corr_profile_enable")
+
+    def profile_read(self, reset: bool = True) -> list[dict]:
+        out = []
+        for a in range(len(self)):
+            prof = Profile()
+            _check(self._lib.corr_profile_read(self._ctx(a), ctypes.byref(prof), int(reset)),
+                   "corr_profile_read")
+            out.append(prof.as_dict())
+        return out
 
     def _ptrs(self, tensors, what):
         arr = (ctypes.c_void_p * len(self))()

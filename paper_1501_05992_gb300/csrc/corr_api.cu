@@ -679,6 +679,16 @@ long long corr_batch_samples(const corr_batch *b, int a)
     return corr_samples(b->ctx[a]);
 }
 
+corr_ctx *corr_batch_array(corr_batch *b, int a)
+{
+    if (!b || a < 0 || a >= b->n) {
+        ret(CORR_E_ARG);
+        return nullptr;
+    }
+    g_last_error = CORR_OK;
+    return b->ctx[a];
+}
+
 int corr_batch_accumulate(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
                           void *stream)
 {
@@ -774,15 +784,8 @@ int corr_batch_graph_capture(corr_batch *b, const uint8_t *const *d_volt, const 
         if (b->ctx[a]->samples != 0) return ret(CORR_E_STATE);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     *graph_exec = nullptr;
-    // capture never records timing events
-    bool prof[CORR_BATCH_MAX];
-    for (int a = 0; a < b->n; ++a) {
-        prof[a] = b->ctx[a]->prof_on;
-        b->ctx[a]->prof_on = false;
-    }
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
-        for (int a = 0; a < b->n; ++a) b->ctx[a]->prof_on = prof[a];
         return ret(CORR_E_CUDA);
     }
     int rc = corr_batch_accumulate(b, d_volt, n_time, stream);
@@ -790,7 +793,6 @@ int corr_batch_graph_capture(corr_batch *b, const uint8_t *const *d_volt, const 
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(s, &graph);
     for (int a = 0; a < b->n; ++a) {
-        b->ctx[a]->prof_on = prof[a];
         b->ctx[a]->samples = 0;       // the captured integration ends with its dump
         b->ctx[a]->fresh = true;
     }
@@ -840,17 +842,19 @@ int corr_profile_read(corr_ctx *c, corr_profile *out, int reset)
     if (!c || !out) return ret(CORR_E_ARG);
     for (int k = 0; k < CORR_K_KINDS; ++k) {
         double ms = 0.0;
+        long long timed = 0;
         for (auto &ev : c->prof_pending[k]) {
             float t = 0.f;
             if (cudaEventSynchronize(ev.second) != cudaSuccess ||
                 cudaEventElapsedTime(&t, ev.first, ev.second) != cudaSuccess) {
-                cudaGetLastError();
-                return ret(CORR_E_CUDA);
+                cudaGetLastError();          // e.g. an event recorded inside a graph
+                continue;
             }
             ms += t;
+            ++timed;
         }
         out->launches[k] = c->prof_launches[k];
-        out->timed[k] = (long long)c->prof_pending[k].size();
+        out->timed[k] = timed;
         out->ms[k] = ms;
         if (reset) {
             for (auto &ev : c->prof_pending[k]) c->prof_pool.push_back(ev);

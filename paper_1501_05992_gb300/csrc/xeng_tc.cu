@@ -91,7 +91,7 @@ constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | (1u << 15) | (1
 struct ArrayParams {
     int32_t *acc;
     int n, n_chan, nt, n_tiles, per_chan, n_stages, item_begin;
-    int zero_invalid, fresh;
+    int fresh;
 };
 
 struct Params {
@@ -304,6 +304,7 @@ __device__ __forceinline__ void codes(uint32_t w, bool zero_invalid, uint32_t &R
     }
 }
 
+template <bool kZeroInvalid>
 __global__ void __launch_bounds__(kThreads, 1)
 xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Params p)
 {
@@ -369,16 +370,16 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             bool ok = true;
             for (int item = first_item; ok && item < p.n_items; item += item_step) {
                 const Item it = decode_item(p, item);
-                const ArrayParams &A = p.a[it.a];
+                const int n_stages = p.a[it.a].n_stages;
                 const CUtensorMap *tmap = &tmaps.m[it.a];
                 const int f = it.f, I = it.I, J = it.J;
                 const bool diag = it.diag;
-                for (int s = 0; s < kPrefetchStages && s < A.n_stages; ++s) {
+                for (int s = 0; s < kPrefetchStages && s < n_stages; ++s) {
                     tma_prefetch_3d(tmap, J * kTile, f, s * kTc);
                     if (!diag) tma_prefetch_3d(tmap, I * kTile, f, s * kTc);
                 }
-                for (int s = 0; s < A.n_stages; ++s) {
-                    if (s + kPrefetchStages < A.n_stages) {
+                for (int s = 0; s < n_stages; ++s) {
+                    if (s + kPrefetchStages < n_stages) {
                         tma_prefetch_3d(tmap, J * kTile, f, (s + kPrefetchStages) * kTc);
                         if (!diag) tma_prefetch_3d(tmap, I * kTile, f, (s + kPrefetchStages) * kTc);
                     }
@@ -476,7 +477,6 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
         for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
             const Item it = decode_item(p, item);
             const int n_stages = p.a[it.a].n_stages;
-            const bool zi = p.a[it.a].zero_invalid != 0;
             const bool diag = it.diag;
             // per-input code sums: byte lanes (<= 16 rows), then 16-bit lanes
             uint32_t b8[2][2][4], s16lo[2][2][4], s16hi[2][2][4];
@@ -502,7 +502,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                     uint32_t R[4], M[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        codes(ww[k], zi, R[k], M[k]);
+                        codes(ww[k], kZeroInvalid, R[k], M[k]);
                         b8[1][0][k] += R[k];
                         b8[1][1][k] += M[k];
                     }
@@ -517,7 +517,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                     uint32_t R[4], M[4];
 #pragma unroll
                     for (int k = 0; k < 4; ++k) {
-                        codes(ww[k], zi, R[k], M[k]);
+                        codes(ww[k], kZeroInvalid, R[k], M[k]);
                         b8[0][0][k] += R[k];
                         b8[0][1][k] += M[k];
                     }
@@ -603,9 +603,12 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
         bool ok = true;
         for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
             const Item it = decode_item(p, item);
-            const ArrayParams &A = p.a[it.a];
-            const long long P = n_pairs(A.n);
-            const int T_eff = A.n_stages * kTc;
+            // copy this array's parameters into registers once per item
+            const int n_in = p.a[it.a].n;
+            const bool fresh = p.a[it.a].fresh != 0;
+            int32_t *const acc = p.a[it.a].acc;
+            const long long P = n_pairs(n_in);
+            const int T_eff = p.a[it.a].n_stages * kTc;
             const int f = it.f, I = it.I, J = it.J;
             const bool diag = it.diag;
             const int buf = local & 1;
@@ -629,7 +632,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             const int Sri = si[sum_slot(il)], Smi = si[kTile + sum_slot(il)];
             const int Ei = Sri + Smi, Di = Smi - Sri;
             const int base_re = 128 * T_eff - 8 * Ei;
-            int32_t *out = A.acc + ((size_t)f * P + (size_t)i * (i + 1) / 2) * 2;
+            int32_t *out = acc + ((size_t)f * P + (size_t)i * (i + 1) / 2) * 2;
             const uint32_t taddr = tmem + uint32_t(buf * 256) + (uint32_t(q * 32) << 16);
 #pragma unroll 1
             for (int c0 = 0; c0 < kTile; c0 += 16) {
@@ -637,7 +640,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 tmem_ld16(taddr + c0, vre);
                 tmem_ld16(taddr + 128 + c0, vim);
                 tmem_wait_ld();
-                if (i < A.n) {
+                if (i < n_in) {
 #pragma unroll
                     for (int k = 0; k < 16; ++k) {
                         const int jl = c0 + k;
@@ -649,7 +652,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                         const int re = pre + base_re - 8 * (Srj + Smj);
                         const int im = pim - 8 * Di + 8 * (Smj - Srj);
                         int2 *dst = reinterpret_cast<int2 *>(out + size_t(j) * 2);
-                        if (A.fresh) {
+                        if (fresh) {
                             *dst = make_int2(re, im);
                         } else {
                             int2 v = *dst;
@@ -721,6 +724,9 @@ bool tc_supported(int n_inputs, int device)
     return cached[device] == 1;
 }
 
+cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, int dev,
+                         DeviceStatus *status, cudaStream_t s);
+
 cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus *status, cudaStream_t s)
 {
     if (count < 0 || count > kMaxArrays) return cudaErrorInvalidValue;
@@ -733,23 +739,41 @@ cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus 
     {
         std::lock_guard<std::mutex> lock(g_dev_mu);
         if (!g_attr_set[dev]) {
-            e = cudaFuncSetAttribute(xeng_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+            e = cudaFuncSetAttribute(xeng_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kSmemBytes);
+            if (e != cudaSuccess) return e;
+            e = cudaFuncSetAttribute(xeng_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     kSmemBytes);
             if (e != cudaSuccess) return e;
             e = cudaDeviceGetAttribute(&g_sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) return e;
             g_attr_set[dev] = 1;
         }
     }
-    // arrays with work, longest items first
-    int order[kMaxArrays], m = 0;
+    // arrays with work, longest items first; the invalid-sample mode is a
+    // property of the kernel, so arrays with different modes go to different
+    // launches
     for (int k = 0; k < count; ++k) {
         const TcArray &A = arrays[k];
         if (A.nt <= 0) continue;
         if (A.nt > kTcMaxSamples || A.n < 16 || A.n % 16 != 0 || A.n_chan < 1 || !A.acc ||
             (reinterpret_cast<uintptr_t>(A.volt) & 15) != 0)
             return cudaErrorInvalidValue;
-        order[m++] = k;
     }
+    for (int mode = 0; mode < 2; ++mode) {
+        e = launch_group(arrays, count, mode == 1, dev, status, s);
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, int dev,
+                         DeviceStatus *status, cudaStream_t s)
+{
+    auto enc = encoder();
+    int order[kMaxArrays], m = 0;
+    for (int k = 0; k < count; ++k)
+        if (arrays[k].nt > 0 && arrays[k].zero_invalid == zero_invalid) order[m++] = k;
     if (m == 0) return cudaSuccess;
     for (int x = 1; x < m; ++x)
         for (int y = x; y > 0 && arrays[order[y]].nt > arrays[order[y - 1]].nt; --y) {
@@ -779,7 +803,6 @@ cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus 
         P.per_chan = P.n_tiles * (P.n_tiles + 1) / 2;
         P.n_stages = (A.nt + kTc - 1) / kTc;
         P.item_begin = int(items);
-        P.zero_invalid = A.zero_invalid ? 1 : 0;
         P.fresh = A.fresh ? 1 : 0;
         items += (long long)A.n_chan * P.per_chan;
     }
@@ -788,7 +811,10 @@ cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus 
     prm.n_items = int(items);
     prm.status = status;
     const int grid = prm.n_items < g_sm_count[dev] ? prm.n_items : g_sm_count[dev];
-    xeng_tc_kernel<<<grid, kThreads, kSmemBytes, s>>>(maps, prm);
+    if (zero_invalid)
+        xeng_tc_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(maps, prm);
+    else
+        xeng_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(maps, prm);
     return cudaGetLastError();
 }
 
