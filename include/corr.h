@@ -119,6 +119,10 @@ int corr_set_flags(corr_ctx *ctx, unsigned flags);
  * word).  The caller allocates at least this many bytes, 256-byte aligned. */
 size_t corr_workspace_bytes(const corr_ctx *ctx);
 
+/* The same figure for a shape, without a context or a device (for planning
+ * and admission control); 0 with CORR_E_ARG on invalid sizes. */
+size_t corr_workspace_bytes_for(int n_inputs, int n_chan, int n_time_per_int);
+
 /* Give the context its workspace (device pointer, caller-owned).  Resets the
  * integration (the accumulators are treated as zero).  CORR_E_ARG if d_ws is
  * NULL, not 256-byte aligned, or bytes < corr_workspace_bytes(). */

@@ -94,6 +94,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_set_tile": ([vp, c_int], c_int),
             "corr_set_flags": ([vp, ctypes.c_uint], c_int),
             "corr_workspace_bytes": ([vp], c_size),
+            "corr_workspace_bytes_for": ([c_int, c_int, c_int], c_size),
             "corr_bind_workspace": ([vp, vp, c_size], c_int),
             "corr_accumulate": ([vp, vp, c_int, vp], c_int),
             "corr_dump": ([vp, vp, vp], c_int),
@@ -154,6 +155,14 @@ def _stream_handle(stream) -> int | None:
 
 def n_pairs(n_inputs: int) -> int:
     return n_inputs * (n_inputs + 1) // 2
+
+
+def workspace_bytes(n_inputs: int, n_chan: int, n_time_per_int: int) -> int:
+    """Device workspace a context of this shape needs (no device required)."""
+    nb = load().corr_workspace_bytes_for(n_inputs, n_chan, n_time_per_int)
+    if nb == 0:
+        raise CorrError(load().corr_last_error(), "corr_workspace_bytes_for")
+    return int(nb)
 
 
 class Correlator:

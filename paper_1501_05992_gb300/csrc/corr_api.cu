@@ -372,6 +372,24 @@ size_t corr_workspace_bytes(const corr_ctx *c)
     return layout_of(c).total;
 }
 
+size_t corr_workspace_bytes_for(int n_inputs, int n_chan, int n_time_per_int)
+{
+    if (n_inputs < 1 || n_chan < 1 || n_time_per_int < 1 || n_inputs > 8192 ||
+        (long long)n_time_per_int * 128LL >= (1LL << 31)) {
+        ret(CORR_E_ARG);
+        return 0;
+    }
+    corr_ctx c;
+    c.n = n_inputs;
+    c.f = n_chan;
+    c.t_max = n_time_per_int;
+    c.dp4a = plan_dp4a(n_inputs, n_chan, n_time_per_int);
+    c.mma = plan_mma(n_inputs, n_chan, n_time_per_int);
+    c.host_chunk = n_time_per_int < kHostChunk ? n_time_per_int : kHostChunk;
+    g_last_error = CORR_OK;
+    return layout_of(&c).total;
+}
+
 int corr_bind_workspace(corr_ctx *c, void *d_ws, size_t bytes)
 {
     if (!c || !d_ws || (reinterpret_cast<uintptr_t>(d_ws) % kAlign) != 0) return ret(CORR_E_ARG);

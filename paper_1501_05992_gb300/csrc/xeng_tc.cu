@@ -254,6 +254,14 @@ __device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
         : "r"(taddr));
 }
 
+__device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
+{
+    asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];\n"
+                 : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+                   "=r"(r[7])
+                 : "r"(taddr));
+}
+
 __device__ __forceinline__ void tmem_wait_ld() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 __device__ __forceinline__ void named_sync(int id, int threads)
@@ -635,31 +643,36 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             int32_t *out = acc + ((size_t)f * P + (size_t)i * (i + 1) / 2) * 2;
             const uint32_t taddr = tmem + uint32_t(buf * 256) + (uint32_t(q * 32) << 16);
 #pragma unroll 1
-            for (int c0 = 0; c0 < kTile; c0 += 16) {
-                uint32_t vre[16], vim[16];
-                tmem_ld16(taddr + c0, vre);
-                tmem_ld16(taddr + 128 + c0, vim);
+            for (int c0 = 0; c0 < kTile; c0 += 8) {
+                uint32_t vre[8], vim[8];
+                tmem_ld8(taddr + c0, vre);
+                tmem_ld8(taddr + 128 + c0, vim);
                 tmem_wait_ld();
-                if (i < n_in) {
+                // columns c0 .. c0 + 7 of row i that lie in the lower triangle
+                const int kmax = i < n_in ? min(7, i - (J * kTile + c0)) : -1;
+                if (kmax >= 0) {
+                    int2 *dst = reinterpret_cast<int2 *>(out) + (J * kTile + c0);
+                    int2 prev[8];
+                    if (!fresh) {
+                        // issue every load of the chunk before the first store
 #pragma unroll
-                    for (int k = 0; k < 16; ++k) {
+                        for (int k = 0; k < 8; ++k)
+                            prev[k] = k <= kmax ? dst[k] : make_int2(0, 0);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; ++k) {
+                        if (k > kmax) continue;
                         const int jl = c0 + k;
-                        const int j = J * kTile + jl;
-                        if (j > i) break;
                         const int Srj = sj[sum_slot(jl)], Smj = sj[kTile + sum_slot(jl)];
                         const int pre = __float2int_rn(__uint_as_float(vre[k]) * 262144.0f);
                         const int pim = __float2int_rn(__uint_as_float(vim[k]) * 262144.0f);
-                        const int re = pre + base_re - 8 * (Srj + Smj);
-                        const int im = pim - 8 * Di + 8 * (Smj - Srj);
-                        int2 *dst = reinterpret_cast<int2 *>(out + size_t(j) * 2);
-                        if (fresh) {
-                            *dst = make_int2(re, im);
-                        } else {
-                            int2 v = *dst;
-                            v.x += re;
-                            v.y += im;
-                            *dst = v;
+                        int re = pre + base_re - 8 * (Srj + Smj);
+                        int im = pim - 8 * Di + 8 * (Smj - Srj);
+                        if (!fresh) {
+                            re += prev[k].x;
+                            im += prev[k].y;
                         }
+                        dst[k] = make_int2(re, im);
                     }
                 }
             }
