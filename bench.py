@@ -137,14 +137,26 @@ def barrier(world):
         dist.barrier()
 
 
-def max_over_ranks(x: float, world: int) -> float:
+def max_over_ranks(x: float, world: int, device: str = "cuda") -> float:
+    """The slowest rank's time: the job is done when every rank is."""
     if world == 1:
         return x
     import torch
     import torch.distributed as dist
-    t = torch.tensor([x], dtype=torch.float64, device="cuda")
+    t = torch.tensor([x], dtype=torch.float64, device=device)
     dist.all_reduce(t, op=dist.ReduceOp.MAX)
     return float(t.item())
+
+
+def rank_array_index(a: int, rank: int) -> int:
+    """Generator stream of array a on this rank: every rank correlates its own
+    data (weak scaling; channels shard across GPUs with no exchange)."""
+    return a + 8 * rank
+
+
+def job_units(step_cmac: int, steps: int, world: int) -> int:
+    """Complex MACs done by the whole job: each rank does the full workload."""
+    return step_cmac * steps * world
 
 
 # ----------------------------------------------------------- CPU baseline ---
@@ -234,6 +246,23 @@ def load_peaks():
                 "sm_max_mhz": 2070.0}, "fallback"
 
 
+def measured_traffic(kernel_src: str, profile_md: str, workload: str):
+    """DRAM bytes per launch from the committed ncu summary, but only while the
+    kernel source still matches the one the counters were taken from."""
+    import hashlib
+    import re
+    try:
+        text = open(profile_md).read()
+        sha = hashlib.sha256(open(kernel_src, "rb").read()).hexdigest()[:16]
+    except OSError:
+        return None
+    m = re.search(r"sha256 prefix `([0-9a-f]{16})`", text)
+    t = re.search(r"traffic_bytes_per_full_band_launch: ([0-9.e+]+)", text)
+    if not m or not t or m.group(1) != sha or workload != "full_band":
+        return None
+    return float(t.group(1))
+
+
 def roofline_for(path, ops_per_launch, avg_ms, peaks, src, sm_count):
     achieved = ops_per_launch / (avg_ms * 1e-3) / 1e12          # Tops/s
     if path == "tc_fp8":
@@ -267,7 +296,7 @@ def run_ours(args, world, rank, local):
     # every rank correlates its own arrays (weak scaling, no exchange)
     volts = []
     for a, (n, f, t) in enumerate(arrays):
-        gen = DeviceGenerator(vg.gauss3_params(seed, n, f, array=a + 8 * rank), dev)
+        gen = DeviceGenerator(vg.gauss3_params(seed, n, f, array=rank_array_index(a, rank)), dev)
         v = torch.empty((t * n_int, f, n), dtype=torch.uint8, device=dev)
         for k in range(n_int):
             gen.fill(v[k * t:(k + 1) * t], t0=k * t)
@@ -342,7 +371,7 @@ def run_ours(args, world, rank, local):
     clk = clocks.stop() if clocks else None
     batch.sync(stream)
     elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), world)
-    value = step_cmac * args.steps * world / (elapsed_ms * 1e-3)
+    value = job_units(step_cmac, args.steps, world) / (elapsed_ms * 1e-3)
 
     if args.mode == "direct":
         prof = batch.profile_read(reset=True)
@@ -378,7 +407,9 @@ def run_ours(args, world, rank, local):
     avg_ms = xe_ms / max(1, xe_timed)
     main_path = paths[max(range(len(arrays)), key=lambda a: arrays[a][0] ** 2 * arrays[a][1] * arrays[a][2])]
     roof = roofline_for(main_path, ops_per_launch, avg_ms, peaks, src, sm_count)
-    roof["traffic"] = None
+    roof["traffic"] = (measured_traffic(os.path.join(ROOT, "paper_1501_05992_gb300", "csrc", "xeng_tc.cu"),
+                                        os.path.join(ROOT, "profiles", "xeng_tc_coarse_channel.md"),
+                                        args.workload) if main_path == "tc_fp8" else None)
     roof["kernel"] = {"cudacore": "xeng_dp4a_kernel", "mma_i8": "xeng_mma8_kernel",
                       "tc_fp8": "xeng_tc_kernel"}[main_path]
     roof["launches_per_step"] = xe_per_step

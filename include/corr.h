@@ -163,8 +163,25 @@ int corr_accumulate_host(corr_ctx *ctx, const uint8_t *h_volt, int n_time, void 
 int corr_dump_host(corr_ctx *ctx, int32_t *h_vis, void *stream);
 
 /* Synchronise `stream`, then report a device-side error recorded by a kernel
- * of this context (CORR_E_TIMEOUT if a bounded wait gave up) or CORR_OK. */
+ * of this context (CORR_E_TIMEOUT if a bounded wait gave up) or CORR_OK.  The
+ * error is cleared once reported.  After CORR_E_TIMEOUT the accumulators hold
+ * a partial sum: dump (and discard) or restore a state before going on. */
 int corr_sync(corr_ctx *ctx, void *stream);
+
+/* Limit, in SM clock cycles, of every wait inside the tensor-core kernel
+ * (between its producer, converter, MMA and epilogue roles).  A wait that
+ * exceeds it records CORR_E_TIMEOUT (reported by corr_sync), and the kernel
+ * drains its copies and MMAs, frees its tensor memory and returns instead of
+ * hanging.  0 restores the default (2^31 cycles, about one second). */
+int corr_set_wait_limit(corr_ctx *ctx, long long cycles);
+
+/* Fault injection for tests, made without any GPU fault: with
+ * CORR_INJECT_STALL the next tensor-core launch of this context first waits
+ * on a barrier that nothing ever completes, so its bounded wait expires and
+ * the launch ends with CORR_E_TIMEOUT.  One-shot; CORR_INJECT_NONE clears. */
+#define CORR_INJECT_NONE 0u
+#define CORR_INJECT_STALL 1u
+int corr_debug_inject(corr_ctx *ctx, unsigned what);
 
 /* ------------------------------------------------------ checkpoint/resume -- */
 

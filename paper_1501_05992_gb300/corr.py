@@ -92,6 +92,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_set_path": ([vp, c_int], c_int),
             "corr_get_path": ([vp], c_int),
             "corr_set_tile": ([vp, c_int], c_int),
+            "corr_set_wait_limit": ([vp, ctypes.c_longlong], c_int),
+            "corr_debug_inject": ([vp, ctypes.c_uint], c_int),
             "corr_set_flags": ([vp, ctypes.c_uint], c_int),
             "corr_workspace_bytes": ([vp], c_size),
             "corr_workspace_bytes_for": ([c_int, c_int, c_int], c_size),
@@ -218,6 +220,14 @@ class Correlator:
     def set_tile(self, tile: int) -> None:
         """CUDA-core tile: 32, 64 or 0 (by shape)."""
         _check(self._lib.corr_set_tile(self._ctx, int(tile)), f"corr_set_tile({tile})")
+
+    def set_wait_limit(self, cycles: int) -> None:
+        """Bounded-wait limit of the tensor-core kernel (SM cycles; 0 = default)."""
+        _check(self._lib.corr_set_wait_limit(self._ctx, int(cycles)), "corr_set_wait_limit")
+
+    def inject_stall(self) -> None:
+        """Test hook: the next tensor-core launch times out on purpose."""
+        _check(self._lib.corr_debug_inject(self._ctx, 1), "corr_debug_inject")
 
     def set_path(self, path: str | int) -> None:
         code = PATHS[path] if isinstance(path, str) else int(path)

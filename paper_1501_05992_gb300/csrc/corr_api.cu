@@ -26,6 +26,8 @@ struct corr_ctx {
     int device = 0, sm_major = 0, sm_minor = 0, sm_count = 0;
     int path = CORR_PATH_AUTO;
     int tile = 0;            // CUDA-core tile (32 or 64), 0 = chosen by shape
+    long long wait_limit = 0;   // device bounded-wait limit (cycles), 0 = default
+    bool inject_stall = false;  // one-shot test hook for the next tensor-core launch
     unsigned flags = 0;
 
     // workspace (caller-owned device memory)
@@ -156,8 +158,12 @@ int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
         for (int t0 = 0; t0 < nt; t0 += kTcMaxSamples) {
             const int ntc = nt - t0 < kTcMaxSamples ? nt - t0 : kTcMaxSamples;
             prof_begin(c, s);
+            TcOptions opt;
+            opt.wait_limit = c->wait_limit;
+            opt.inject_stall = c->inject_stall;
+            c->inject_stall = false;
             e = launch_xeng_tc(volt + size_t(t0) * row, c->f, c->n, ntc, zi, c->acc, fresh,
-                               c->status, s);
+                               c->status, opt, s);
             prof_end(c, CORR_K_XENGINE, s, 1);
             if (e != cudaSuccess) return cuda_fail(e);
             fresh = false;
@@ -344,6 +350,20 @@ int corr_set_tile(corr_ctx *c, int tile)
     if (!c || (tile != 0 && tile != 32 && tile != 64)) return ret(CORR_E_ARG);
     if (c->samples != 0) return ret(CORR_E_STATE);
     c->tile = tile;
+    return ret(CORR_OK);
+}
+
+int corr_set_wait_limit(corr_ctx *c, long long cycles)
+{
+    if (!c || cycles < 0) return ret(CORR_E_ARG);
+    c->wait_limit = cycles;
+    return ret(CORR_OK);
+}
+
+int corr_debug_inject(corr_ctx *c, unsigned what)
+{
+    if (!c || what > CORR_INJECT_STALL) return ret(CORR_E_ARG);
+    c->inject_stall = what == CORR_INJECT_STALL;
     return ret(CORR_OK);
 }
 
@@ -748,8 +768,12 @@ int corr_batch_accumulate(corr_batch *b, const uint8_t *const *d_volt, const int
                 arr[k].fresh = t0 == 0 ? c->fresh : false;
                 ++k;
             }
+            TcOptions opt;
+            opt.wait_limit = lead->wait_limit;
+            opt.inject_stall = lead->inject_stall;
+            lead->inject_stall = false;
             prof_begin(lead, s);
-            cudaError_t e = launch_xeng_tc_batch(arr, k, lead->status, s);
+            cudaError_t e = launch_xeng_tc_batch(arr, k, lead->status, opt, s);
             prof_end(lead, CORR_K_XENGINE, s, 1);
             if (e != cudaSuccess) return ret(cuda_fail(e));
         }

@@ -77,6 +77,10 @@ cudaError_t launch_xeng_mma8(const int8_t *X, const int8_t *Xt, int n, int n_pad
 
 // tcgen05 FP8 X-engine straight from packed voltages (no staging).
 bool tc_supported(int n_inputs, int device);
+struct TcOptions {
+    long long wait_limit = 0;   // bounded-wait limit in clock64 cycles (0: about 1 s)
+    bool inject_stall = false;  // test hook: make the launch's first wait expire
+};
 struct TcArray {
     const uint8_t *volt;   // [nt][n_chan][n] packed voltages
     int32_t *acc;          // [n_chan][P][2] accumulators
@@ -86,9 +90,10 @@ struct TcArray {
 // One persistent launch over every (channel, tile pair) of up to
 // kTcMaxArrays arrays (nt <= kTcMaxSamples each; arrays with nt == 0 skipped).
 cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus *status,
-                                 cudaStream_t s);
+                                 const TcOptions &opt, cudaStream_t s);
 cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool zero_invalid,
-                           int32_t *acc, bool fresh, DeviceStatus *status, cudaStream_t s);
+                           int32_t *acc, bool fresh, DeviceStatus *status, const TcOptions &opt,
+                           cudaStream_t s);
 
 // Record `status` as the calling thread's last error and return it.
 int set_last_error(int status);

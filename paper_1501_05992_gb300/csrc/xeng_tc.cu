@@ -68,7 +68,7 @@ constexpr int kConvWarps = 16, kEpiWarps = 4;
 constexpr int kThreads = (2 + kConvWarps + kEpiWarps) * 32;   // 704
 constexpr int kFirstConvWarp = 2, kFirstEpiWarp = 2 + kConvWarps;
 constexpr int kTmemCols = 512;               // 2 accumulator buffers x (128 Re + 128 Im)
-constexpr long long kWaitLimit = 1LL << 31;  // clock64 cycles (about 1 s)
+constexpr long long kDefaultWaitLimit = 1LL << 31;  // clock64 cycles (about 1 s)
 
 // shared-memory map (offsets from a 1024-aligned base)
 constexpr int kSmPacked = 0;
@@ -76,7 +76,7 @@ constexpr int kSmPlanes = kSmPacked + kPackedStages * kPackedStageBytes;        
 constexpr int kSmSums = kSmPlanes + kPlaneStages * kPlaneStageBytes;              // +120 KB
 constexpr int kSumsBytes = 2 * 2 * 2 * kTile * 4;                                 // [buf][tile][r/m][slot]
 constexpr int kSmBars = kSmSums + kSumsBytes;
-constexpr int kNumBars = 2 * kPackedStages + 2 * kPlaneStages + 4 + 4 + 1;
+constexpr int kNumBars = 2 * kPackedStages + 2 * kPlaneStages + 4 + 4 + 2;
 constexpr int kSmMisc = kSmBars + kNumBars * 8;
 constexpr int kSmemBytes = kSmMisc + 64 + 1024;                                   // + alignment slack
 
@@ -98,6 +98,8 @@ struct Params {
     ArrayParams a[kMaxArrays];
     int n_arrays, n_items;
     DeviceStatus *status;
+    long long wait_limit;   // bounded-wait limit, clock64 cycles
+    int inject_stall;       // test hook: the epilogue first waits on a barrier nobody arrives on
 };
 
 struct Tmaps {
@@ -140,14 +142,14 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
 
 // Bounded wait.  Returns false on timeout or if another role aborted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort,
-                                          DeviceStatus *status, int where)
+                                          DeviceStatus *status, int where, long long limit)
 {
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
         if (mbar_try(bar, parity)) return true;
         if (*abort) return false;
-        if (clock64() - t0 > kWaitLimit) {
+        if (clock64() - t0 > limit) {
             *abort = 1;
             if (atomicCAS(&status->code, 0, CORR_E_TIMEOUT) == 0) {
                 status->where = where;
@@ -162,7 +164,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
 // lane confirms once, so each lane gets the barrier's acquire ordering while
 // only one lane keeps hitting shared memory.
 __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatile int *abort,
-                                          DeviceStatus *status, int where, int lane,
+                                          DeviceStatus *status, int where, int lane, long long limit,
                                           unsigned sleep_ns = 0)
 {
     int ok = 1;
@@ -175,7 +177,7 @@ __device__ __forceinline__ bool warp_wait(uint32_t bar, uint32_t parity, volatil
                     ok = 0;
                     break;
                 }
-                if (clock64() - t0 > kWaitLimit) {
+                if (clock64() - t0 > limit) {
                     *abort = 1;
                     if (atomicCAS(&status->code, 0, CORR_E_TIMEOUT) == 0) {
                         status->where = where;
@@ -332,6 +334,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
     auto bar_sums_full = [&](int b) { return bars + 8u * (2 * kPackedStages + 2 * kPlaneStages + 4 + b); };
     auto bar_sums_empty = [&](int b) { return bars + 8u * (2 * kPackedStages + 2 * kPlaneStages + 6 + b); };
     const uint32_t bar_drain = bars + 8u * (2 * kPackedStages + 2 * kPlaneStages + 8);
+    const uint32_t bar_never = bars + 8u * (2 * kPackedStages + 2 * kPlaneStages + 9);
     uint32_t *tmem_slot = reinterpret_cast<uint32_t *>(smem + kSmMisc);
     volatile int *abort = reinterpret_cast<volatile int *>(smem + kSmMisc + 8);
     volatile int *epi_ok = reinterpret_cast<volatile int *>(smem + kSmMisc + 16);
@@ -352,6 +355,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             mbar_init(bar_sums_empty(b), kEpiWarps);
         }
         mbar_init(bar_drain, 1);
+        mbar_init(bar_never, 1);
         *abort = 0;
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
         for (int a = 0; a < p.n_arrays; ++a)
@@ -391,7 +395,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                         tma_prefetch_3d(tmap, J * kTile, f, (s + kPrefetchStages) * kTc);
                         if (!diag) tma_prefetch_3d(tmap, I * kTile, f, (s + kPrefetchStages) * kTc);
                     }
-                    if (!mbar_wait(bar_packed_empty(stage), phase ^ 1u, abort, p.status, 1)) {
+                    if (!mbar_wait(bar_packed_empty(stage), phase ^ 1u, abort, p.status, 1, p.wait_limit)) {
                         ok = false;
                         break;
                     }
@@ -412,7 +416,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             for (int k = 0; k < kPackedStages; ++k) {
                 if (!((issued >> k) & 1u)) continue;
                 const long long t0 = clock64();
-                while (!mbar_try(bar_packed_full(k), (issued_phase >> k) & 1u) && clock64() - t0 < kWaitLimit) {
+                while (!mbar_try(bar_packed_full(k), (issued_phase >> k) & 1u) && clock64() - t0 < p.wait_limit) {
                 }
             }
         }
@@ -429,7 +433,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 const int n_stages = p.a[it.a].n_stages;
                 const bool diag = it.diag;
                 const int buf = local & 1;
-                if (!mbar_wait(bar_acc_empty(buf), ((acc_phase >> buf) & 1u) ^ 1u, abort, p.status, 2)) {
+                if (!mbar_wait(bar_acc_empty(buf), ((acc_phase >> buf) & 1u) ^ 1u, abort, p.status, 2, p.wait_limit)) {
                     ok = false;
                     break;
                 }
@@ -438,7 +442,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 const uint32_t d_tmem = tmem + uint32_t(buf * 256);
                 uint32_t accum = 0;
                 for (int s = 0; s < n_stages; ++s) {
-                    if (!mbar_wait(bar_plane_full(stage), phase, abort, p.status, 3)) {
+                    if (!mbar_wait(bar_plane_full(stage), phase, abort, p.status, 3, p.wait_limit)) {
                         ok = false;
                         break;
                     }
@@ -467,7 +471,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             // drain all MMAs issued by this thread before TMEM is released
             mma_commit(bar_drain);
             const long long t0 = clock64();
-            while (!mbar_try(bar_drain, 0) && clock64() - t0 < kWaitLimit) {
+            while (!mbar_try(bar_drain, 0) && clock64() - t0 < p.wait_limit) {
             }
         }
     } else if (warp < kFirstEpiWarp) {
@@ -495,8 +499,8 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
 #pragma unroll
                     for (int k = 0; k < 4; ++k) b8[t][q][k] = s16lo[t][q][k] = s16hi[t][q][k] = 0;
             for (int s = 0; s < n_stages; ++s) {
-                if (!mbar_wait(bar_packed_full(pstage), pphase, abort, p.status, 4) ||
-                    !mbar_wait(bar_plane_empty(cstage), cphase ^ 1u, abort, p.status, 5)) {
+                if (!mbar_wait(bar_packed_full(pstage), pphase, abort, p.status, 4, p.wait_limit) ||
+                    !mbar_wait(bar_plane_empty(cstage), cphase ^ 1u, abort, p.status, 5, p.wait_limit)) {
                     ok = false;
                     break;
                 }
@@ -576,7 +580,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                         s16hi[t][q][k] += __shfl_xor_sync(0xFFFFFFFFu, s16hi[t][q][k], 16);
                     }
             const int buf = local & 1;
-            if (!warp_wait(bar_sums_empty(buf), ((sphase >> buf) & 1u) ^ 1u, abort, p.status, 6, lane, 64)) {
+            if (!warp_wait(bar_sums_empty(buf), ((sphase >> buf) & 1u) ^ 1u, abort, p.status, 6, lane, p.wait_limit, 64)) {
                 ok = false;
                 break;
             }
@@ -609,6 +613,15 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
         uint32_t aphase = 0;                          // bit b: phase of buffer b
         int local = 0;
         bool ok = true;
+        if (p.inject_stall) {
+            // test hook: a wait that nothing ever satisfies; it must expire, record
+            // CORR_E_TIMEOUT and take every role of the CTA down the abort path
+            const bool mine = warp_wait(bar_never, 0, abort, p.status, 9, lane, p.wait_limit, 64);
+            if (lane == 0) epi_ok[q] = mine ? 1 : 0;
+            named_sync(2, kEpiWarps * 32);
+            ok = epi_ok[0] && epi_ok[1] && epi_ok[2] && epi_ok[3];
+            named_sync(2, kEpiWarps * 32);
+        }
         for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
             const Item it = decode_item(p, item);
             // copy this array's parameters into registers once per item
@@ -623,8 +636,8 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             // the four epilogue warps decide together whether to go on, so that
             // none of them is ever left waiting at a named barrier
             const uint32_t ph = (aphase >> buf) & 1u;
-            const bool mine = warp_wait(bar_acc_full(buf), ph, abort, p.status, 7, lane, 256) &&
-                              warp_wait(bar_sums_full(buf), ph, abort, p.status, 8, lane, 64);
+            const bool mine = warp_wait(bar_acc_full(buf), ph, abort, p.status, 7, lane, p.wait_limit, 256) &&
+                              warp_wait(bar_sums_full(buf), ph, abort, p.status, 8, lane, p.wait_limit, 64);
             if (lane == 0) epi_ok[q] = mine ? 1 : 0;
             named_sync(2, kEpiWarps * 32);
             ok = epi_ok[0] && epi_ok[1] && epi_ok[2] && epi_ok[3];
@@ -738,9 +751,10 @@ bool tc_supported(int n_inputs, int device)
 }
 
 cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, int dev,
-                         DeviceStatus *status, cudaStream_t s);
+                         DeviceStatus *status, const TcOptions &opt, cudaStream_t s);
 
-cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus *status, cudaStream_t s)
+cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus *status,
+                                 const TcOptions &opt, cudaStream_t s)
 {
     if (count < 0 || count > kMaxArrays) return cudaErrorInvalidValue;
     auto enc = encoder();
@@ -774,14 +788,14 @@ cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus 
             return cudaErrorInvalidValue;
     }
     for (int mode = 0; mode < 2; ++mode) {
-        e = launch_group(arrays, count, mode == 1, dev, status, s);
+        e = launch_group(arrays, count, mode == 1, dev, status, opt, s);
         if (e != cudaSuccess) return e;
     }
     return cudaSuccess;
 }
 
 cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, int dev,
-                         DeviceStatus *status, cudaStream_t s)
+                         DeviceStatus *status, const TcOptions &opt, cudaStream_t s)
 {
     auto enc = encoder();
     int order[kMaxArrays], m = 0;
@@ -823,6 +837,8 @@ cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, in
     prm.n_arrays = m;
     prm.n_items = int(items);
     prm.status = status;
+    prm.wait_limit = opt.wait_limit > 0 ? opt.wait_limit : kDefaultWaitLimit;
+    prm.inject_stall = opt.inject_stall ? 1 : 0;
     const int grid = prm.n_items < g_sm_count[dev] ? prm.n_items : g_sm_count[dev];
     if (zero_invalid)
         xeng_tc_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(maps, prm);
@@ -832,10 +848,11 @@ cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, in
 }
 
 cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool zero_invalid,
-                           int32_t *acc, bool fresh, DeviceStatus *status, cudaStream_t s)
+                           int32_t *acc, bool fresh, DeviceStatus *status, const TcOptions &opt,
+                           cudaStream_t s)
 {
     const TcArray a{volt, acc, n_chan, n, nt, zero_invalid, fresh};
-    return launch_xeng_tc_batch(&a, 1, status, s);
+    return launch_xeng_tc_batch(&a, 1, status, opt, s);
 }
 
 }  // namespace corr
