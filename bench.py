@@ -305,8 +305,7 @@ def run_ours(args, world, rank, local):
              for n, f, t in arrays]
     tuned = None
     if args.autotune:
-        cache = os.path.join(ROOT, "gpurun_out", "autotune_cache.json") \
-            if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None
+        cache = os.environ.get("CORR_AUTOTUNE_CACHE") or None
         specs = autotune.plan(specs, cache_path=cache)
         tuned = [{k: s[k] for k in ("path", "tile")} for s in specs]
     batch = corr.Batch(specs, device=dev)
