@@ -152,17 +152,25 @@ long long corr_samples(const corr_ctx *ctx);
 /*
  * End-to-end variants over HOST buffers: h_volt is host memory
  * [n_time][n_chan][n_inputs] (pinned memory gives full copy bandwidth); the
- * library copies it through the workspace's device staging ring in chunks,
- * overlapping each chunk's host-to-device copy with the previous chunk's
- * correlation, all on `stream`.  corr_dump_host copies the triangle to host
- * memory h_vis.  Both are asynchronous like their device counterparts: the
- * host buffers must stay valid and unmodified until the stream reaches the
- * end of the enqueued work.
+ * library copies it in chunks of up to 500 samples through a ring of three
+ * device staging buffers in the workspace, on its own copy stream, so that
+ * each chunk's host-to-device copy overlaps the correlation of the previous
+ * ones on `stream`.  h_volt must stay valid and unmodified until `stream`
+ * has passed the call.
+ *
+ * corr_dump_host copies the triangle to host memory h_vis (int32
+ * [n_chan][P][2]) and starts a new integration.  The device-to-host copy runs
+ * on the context's own output stream, after the work already enqueued on
+ * `stream`, so the next integration's correlation overlaps it (the first
+ * later write of the accumulators waits for it).  h_vis is complete once
+ * corr_sync(ctx, stream) has returned (or the device is synchronised); it
+ * must not be read or reused before then.
  */
 int corr_accumulate_host(corr_ctx *ctx, const uint8_t *h_volt, int n_time, void *stream);
 int corr_dump_host(corr_ctx *ctx, int32_t *h_vis, void *stream);
 
-/* Synchronise `stream`, then report a device-side error recorded by a kernel
+/* Synchronise `stream` and the context's output stream (host dumps), then
+ * report a device-side error recorded by a kernel
  * of this context (CORR_E_TIMEOUT if a bounded wait gave up) or CORR_OK.  The
  * error is cleared once reported.  After CORR_E_TIMEOUT the accumulators hold
  * a partial sum: dump (and discard) or restore a state before going on. */

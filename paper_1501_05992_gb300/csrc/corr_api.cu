@@ -36,17 +36,21 @@ struct corr_ctx {
     DeviceStatus *status = nullptr;
     int32_t *acc = nullptr;
     uint8_t *stage = nullptr;
-    uint8_t *host_stage[2] = {nullptr, nullptr};
+    uint8_t *host_stage[kHostBuffers] = {};
 
     StagePlan dp4a{}, mma{};
     int host_chunk = 0;
+    int host_next = 0;     // staging buffer of the next host chunk (rotates across calls)
 
     long long samples = 0;
     bool fresh = true;     // accumulators hold no data: next X-engine stores
 
-    cudaStream_t copy_stream = nullptr;
-    cudaEvent_t ev_full[2] = {nullptr, nullptr};
-    cudaEvent_t ev_free[2] = {nullptr, nullptr};
+    cudaStream_t copy_stream = nullptr;             // host -> device chunk copies
+    cudaEvent_t ev_full[kHostBuffers] = {};
+    cudaEvent_t ev_free[kHostBuffers] = {};
+    cudaStream_t out_stream = nullptr;              // device -> host dump copies
+    cudaEvent_t ev_dumped = nullptr, ev_out_free = nullptr;
+    bool out_pending = false;  // a host dump may still be reading the accumulators
 
     // profiling: launch counts (always) and event pairs (when enabled)
     bool prof_on = false;
@@ -67,7 +71,7 @@ int ret(int status)
 }
 
 struct WsLayout {
-    size_t status_off, acc_off, stage_off, host_off[2], total;
+    size_t status_off, acc_off, stage_off, host_off[kHostBuffers], total;
 };
 
 size_t acc_words(const corr_ctx *c) { return size_t(c->f) * size_t(n_pairs(c->n)) * 2; }
@@ -84,7 +88,7 @@ WsLayout layout_of(const corr_ctx *c)
     const size_t stage = c->dp4a.bytes > c->mma.bytes ? c->dp4a.bytes : c->mma.bytes;
     off = round_up(off + stage, kAlign);
     const size_t host = size_t(c->host_chunk) * size_t(c->f) * size_t(c->n);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kHostBuffers; ++b) {
         L.host_off[b] = off;
         off = round_up(off + host, kAlign);
     }
@@ -146,9 +150,22 @@ void prof_end(corr_ctx *c, int kind, cudaStream_t s, int launches)
     c->prof_cur = {nullptr, nullptr};
 }
 
+// Order `s` after a host dump that may still be reading the accumulators.
+int wait_host_dump(corr_ctx *c, cudaStream_t s)
+{
+    if (!c->out_pending) return CORR_OK;
+    if (cudaStreamWaitEvent(s, c->ev_out_free, 0) != cudaSuccess) {
+        cudaGetLastError();
+        return CORR_E_CUDA;
+    }
+    c->out_pending = false;
+    return CORR_OK;
+}
+
 // Correlate n_time samples already in device memory.
 int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
 {
+    if (wait_host_dump(c, s) != CORR_OK) return CORR_E_CUDA;
     const int path = resolve_path(c, c->path);
     const bool zi = (c->flags & CORR_ZERO_INVALID) != 0;
     bool fresh = c->fresh;
@@ -299,13 +316,16 @@ corr_ctx *corr_create(int n_inputs, int n_chan, int n_time_per_int)
     c->dp4a = plan_dp4a(n_inputs, n_chan, n_time_per_int);
     c->mma = plan_mma(n_inputs, n_chan, n_time_per_int);
     c->host_chunk = n_time_per_int < kHostChunk ? n_time_per_int : kHostChunk;
-    if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (cudaStreamCreateWithFlags(&c->copy_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaStreamCreateWithFlags(&c->out_stream, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_dumped, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&c->ev_out_free, cudaEventDisableTiming) != cudaSuccess) {
         cudaGetLastError();
-        delete c;
+        corr_destroy(c);
         ret(CORR_E_CUDA);
         return nullptr;
     }
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kHostBuffers; ++b) {
         if (cudaEventCreateWithFlags(&c->ev_full[b], cudaEventDisableTiming) != cudaSuccess ||
             cudaEventCreateWithFlags(&c->ev_free[b], cudaEventDisableTiming) != cudaSuccess) {
             cudaGetLastError();
@@ -321,11 +341,14 @@ corr_ctx *corr_create(int n_inputs, int n_chan, int n_time_per_int)
 int corr_destroy(corr_ctx *c)
 {
     if (!c) return ret(CORR_E_ARG);
-    for (int b = 0; b < 2; ++b) {
+    for (int b = 0; b < kHostBuffers; ++b) {
         if (c->ev_full[b]) cudaEventDestroy(c->ev_full[b]);
         if (c->ev_free[b]) cudaEventDestroy(c->ev_free[b]);
     }
+    if (c->ev_dumped) cudaEventDestroy(c->ev_dumped);
+    if (c->ev_out_free) cudaEventDestroy(c->ev_out_free);
     if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+    if (c->out_stream) cudaStreamDestroy(c->out_stream);
     for (int k = 0; k < CORR_K_KINDS; ++k)
         for (auto &ev : c->prof_pending[k]) c->prof_pool.push_back(ev);
     for (auto &ev : c->prof_pool) {
@@ -420,8 +443,9 @@ int corr_bind_workspace(corr_ctx *c, void *d_ws, size_t bytes)
     c->status = reinterpret_cast<DeviceStatus *>(c->ws + L.status_off);
     c->acc = reinterpret_cast<int32_t *>(c->ws + L.acc_off);
     c->stage = c->ws + L.stage_off;
-    c->host_stage[0] = c->ws + L.host_off[0];
-    c->host_stage[1] = c->ws + L.host_off[1];
+    for (int b = 0; b < kHostBuffers; ++b) c->host_stage[b] = c->ws + L.host_off[b];
+    c->host_next = 0;
+    c->out_pending = false;
     c->samples = 0;
     c->fresh = true;
     if (cudaMemset(c->status, 0, sizeof(DeviceStatus)) != cudaSuccess) {
@@ -478,10 +502,10 @@ int corr_accumulate_host(corr_ctx *c, const uint8_t *h_volt, int n_time, void *s
     if (c->samples + n_time > c->t_max) return ret(CORR_E_OVERFLOW);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t row = size_t(c->f) * size_t(c->n);
-    int k = 0;
-    for (int t0 = 0; t0 < n_time; t0 += c->host_chunk, ++k) {
+    for (int t0 = 0; t0 < n_time; t0 += c->host_chunk) {
         const int ntc = n_time - t0 < c->host_chunk ? n_time - t0 : c->host_chunk;
-        const int b = k & 1;
+        const int b = c->host_next;
+        c->host_next = (b + 1) % kHostBuffers;
         if (cudaStreamWaitEvent(c->copy_stream, c->ev_free[b], 0) != cudaSuccess ||
             cudaMemcpyAsync(c->host_stage[b], h_volt + size_t(t0) * row, size_t(ntc) * row,
                             cudaMemcpyHostToDevice, c->copy_stream) != cudaSuccess ||
@@ -511,10 +535,17 @@ int corr_dump_host(corr_ctx *c, int32_t *h_vis, void *stream)
         cudaGetLastError();
         return ret(CORR_E_CUDA);
     }
-    if (cudaMemcpyAsync(h_vis, c->acc, bytes, cudaMemcpyDeviceToHost, s) != cudaSuccess) {
+    // the copy runs on the output stream, so the correlation work that follows
+    // on `stream` (the next integration's host chunks) overlaps it; the next
+    // write of the accumulators waits for it (out_pending)
+    if (cudaEventRecord(c->ev_dumped, s) != cudaSuccess ||
+        cudaStreamWaitEvent(c->out_stream, c->ev_dumped, 0) != cudaSuccess ||
+        cudaMemcpyAsync(h_vis, c->acc, bytes, cudaMemcpyDeviceToHost, c->out_stream) != cudaSuccess ||
+        cudaEventRecord(c->ev_out_free, c->out_stream) != cudaSuccess) {
         cudaGetLastError();
         return ret(CORR_E_CUDA);
     }
+    c->out_pending = true;
     c->fresh = true;
     c->samples = 0;
     return ret(CORR_OK);
@@ -523,7 +554,8 @@ int corr_dump_host(corr_ctx *c, int32_t *h_vis, void *stream)
 int corr_sync(corr_ctx *c, void *stream)
 {
     if (!c) return ret(CORR_E_ARG);
-    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess) {
+    if (cudaStreamSynchronize(static_cast<cudaStream_t>(stream)) != cudaSuccess ||
+        (c->out_stream && cudaStreamSynchronize(c->out_stream) != cudaSuccess)) {
         cudaGetLastError();
         return ret(CORR_E_CUDA);
     }
@@ -596,6 +628,7 @@ int corr_set_state(corr_ctx *c, const void *h_buf, size_t bytes, void *stream)
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const uint8_t *src = static_cast<const uint8_t *>(h_buf) + sizeof(h);
     const size_t nb = acc_words(c) * sizeof(int32_t);
+    if (wait_host_dump(c, s) != CORR_OK) return ret(CORR_E_CUDA);
     if (cudaMemcpyAsync(c->acc, src, nb, cudaMemcpyHostToDevice, s) != cudaSuccess ||
         cudaStreamSynchronize(s) != cudaSuccess) {
         cudaGetLastError();

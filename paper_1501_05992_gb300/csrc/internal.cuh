@@ -17,6 +17,7 @@ constexpr int kMmaTile = 64;           // int8 mma.sync tile (inputs per side)
 constexpr int kMmaKT = 64;             // samples per K stage of the mma.sync kernel
 constexpr size_t kStageCap = size_t(1) << 30;  // unpacked-operand staging cap, bytes
 constexpr int kHostChunk = 500;        // samples per host->device transfer chunk
+constexpr int kHostBuffers = 3;        // device staging buffers of the host chunks
 constexpr int kTcMaxSamples = 32768;   // tcgen05 path: samples per launch (FP32 sums < 2^24)
 constexpr int kTcMaxArrays = 4;        // tcgen05 path: arrays correlated by one launch
 constexpr size_t kAlign = 256;

@@ -132,6 +132,52 @@ def test_host_buffers_exact(path):
     assert np.array_equal(correlate(volt, path, host=True, chunks=[(0, 1), (1, 1234)]), want)
 
 
+@pytest.mark.parametrize("path", ALL_PATHS)
+def test_back_to_back_host_integrations(path):
+    """Host dumps run on the context's output stream while the next
+    integration is already being correlated: every dump must still hold its
+    own integration, including a device dump and a state restore that follow
+    a host dump without any synchronisation in between."""
+    N, F, T = 128, 6, 1700
+    if not path_available(path, N):
+        pytest.skip(f"{path} unsupported")
+    rng = np.random.default_rng(81)
+    volts = [rng.integers(0, 256, (T, F, N), dtype=np.uint8) for _ in range(4)]
+    wants = [oracle.to_int32(oracle.xmac(v)) for v in volts]
+    hv = [torch.from_numpy(v).pin_memory() for v in volts]
+    P = N * (N + 1) // 2
+    outs = [torch.full((F, P, 2), -5, dtype=torch.int32).pin_memory() for _ in range(3)]
+    d3 = torch.from_numpy(volts[3]).cuda()
+    c = corr.Correlator(N, F, T, path=path)
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    c.accumulate_host(hv[0], stream=s)
+    c.dump_host(outs[0], stream=s)
+    c.accumulate_host(hv[1][:900], stream=s)
+    c.accumulate_host(hv[1][900:], stream=s)
+    c.dump_host(outs[1], stream=s)
+    c.accumulate_host(hv[2], stream=s)
+    dv = c.dump(stream=s)                        # device dump right after a host dump
+    c.accumulate(d3, stream=s)
+    c.dump_host(outs[2], stream=s)
+    c.sync(s)
+    assert np.array_equal(outs[0].numpy(), wants[0])
+    assert np.array_equal(outs[1].numpy(), wants[1])
+    assert np.array_equal(dv.cpu().numpy(), wants[2])
+    assert np.array_equal(outs[2].numpy(), wants[3])
+    # a restore right after a host dump must not race the copy out
+    c.accumulate_host(hv[0][:1000], stream=s)
+    state = c.get_state(stream=s)
+    c.dump_host(outs[0], stream=s)
+    c.set_state(state, stream=s)
+    c.accumulate_host(hv[0][1000:], stream=s)
+    c.dump_host(outs[1], stream=s)
+    c.sync(s)
+    assert np.array_equal(outs[0].numpy(), oracle.to_int32(oracle.xmac(volts[0][:1000])))
+    assert np.array_equal(outs[1].numpy(), wants[0])
+    c.close()
+
+
 def test_overflow_and_state_errors():
     c = corr.Correlator(16, 2, 100, path="cudacore")
     v = torch.zeros((60, 2, 16), dtype=torch.uint8, device="cuda")
