@@ -35,7 +35,10 @@
 //   warp 0     TMA producer: packed bytes [64 samples][128 inputs] per tile,
 //              with L2 prefetch of the tiles kPrefetchStages stages ahead
 //   warp 1     TMEM allocator and single-thread MMA issuer
-//   warps 2-17 converters: packed bytes -> E4M3 planes (+ per-input sums)
+//   warps 2-17 converters: packed bytes -> E4M3 planes (+ per-input sums), as
+//              two teams of 8 warps that take alternate 64-sample stages (a
+//              warp's barrier waits and arrivals cost about as much as its
+//              conversion work, so a team owning whole stages halves that cost)
 //   warps 18-21 epilogue: TMEM -> int32, corrections, packed-triangle store
 // Accumulators are double-buffered in TMEM (2 x 256 columns) so the epilogue
 // of one item overlaps the main loop of the next.  Every wait is bounded: on
@@ -65,6 +68,15 @@ constexpr int kOffRI = 0, kOffMI = kPlaneBytes, kOffMJ = 2 * kPlaneBytes, kOffRJ
               kOffNMJ = 4 * kPlaneBytes;
 constexpr int kPlaneStageBytes = 5 * kPlaneBytes;  // 40 KB
 constexpr int kConvWarps = 16, kEpiWarps = 4;
+constexpr int kTeams = 2, kTeamWarps = kConvWarps / kTeams;   // converter teams own alternate stages
+// A team waits on the packed slot of stage g with the parity of g's use of the
+// slot.  That is unambiguous only if the slot's previous use (g - kPackedStages)
+// was the same team's, already consumed: with a slot count that is not a
+// multiple of the team count the previous use is the other team's, its copy
+// may still be in flight, and the parity of use g would match the completed
+// use g - 2 kPackedStages.  (Plane slots are waited on by the in-order MMA
+// issuer, and their "empty" waits are ordered by it, so any count works.)
+static_assert(kPackedStages % kTeams == 0, "packed slots must be team-exclusive");
 constexpr int kThreads = (2 + kConvWarps + kEpiWarps) * 32;   // 704
 constexpr int kFirstConvWarp = 2, kFirstEpiWarp = 2 + kConvWarps;
 constexpr int kTmemCols = 512;               // 2 accumulator buffers x (128 Re + 128 Im)
@@ -72,7 +84,7 @@ constexpr long long kDefaultWaitLimit = 1LL << 31;  // clock64 cycles (about 1 s
 
 // shared-memory map (offsets from a 1024-aligned base)
 constexpr int kSmPacked = 0;
-constexpr int kSmPlanes = kSmPacked + kPackedStages * kPackedStageBytes;          // 64 KB
+constexpr int kSmPlanes = kSmPacked + kPackedStages * kPackedStageBytes;          // 96 KB
 constexpr int kSmSums = kSmPlanes + kPlaneStages * kPlaneStageBytes;              // +120 KB
 constexpr int kSumsBytes = 2 * 2 * 2 * kTile * 4;                                 // [buf][tile][r/m][slot]
 constexpr int kSmBars = kSmSums + kSumsBytes;
@@ -342,10 +354,10 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
     if (threadIdx.x == 0) {
         for (int s = 0; s < kPackedStages; ++s) {
             mbar_init(bar_packed_full(s), 1);
-            mbar_init(bar_packed_empty(s), kConvWarps);
+            mbar_init(bar_packed_empty(s), kTeamWarps);
         }
         for (int s = 0; s < kPlaneStages; ++s) {
-            mbar_init(bar_plane_full(s), kConvWarps);
+            mbar_init(bar_plane_full(s), kTeamWarps);
             mbar_init(bar_plane_empty(s), 1);
         }
         for (int b = 0; b < 2; ++b) {
@@ -476,65 +488,70 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
         }
     } else if (warp < kFirstEpiWarp) {
         // ----------------------------------------------------- converters --
-        // thread ct owns chunk column c (16 inputs) of one row (sample) of each
-        // stage, for both tiles, so its per-input sums never leave registers
-        const int ct = threadIdx.x - kFirstConvWarp * 32;        // 0..511
-        const int c = ct & 7, row = ct >> 3;                      // chunk column, row 0..63
-        const uint32_t so = uint32_t(row * 128 + ((c ^ (row & 7)) << 4));   // swizzled plane offset
-        const uint32_t po = uint32_t(row * 128 + c * 16);                   // packed offset
-        int pstage = 0, cstage = 0;
-        uint32_t pphase = 0, cphase = 0, sphase = 0;
+        // Two teams of kTeamWarps warps; team t converts the stages g (counted
+        // over all items of this CTA) with g % 2 == t, so each warp spends its
+        // barrier latency once per two stages.  Thread u of a team owns chunk
+        // column c (16 inputs) of one tile and a set of rows of each of its
+        // stages, so its per-input sums cover 16 inputs and stay in registers:
+        //   off-diagonal item: q < 16 -> J tile, q >= 16 -> I tile, rows (q & 15) + 16k, k < 4
+        //   diagonal item:     J tile, rows q + 32k, k < 2
+        const int team = (warp - kFirstConvWarp) / kTeamWarps;
+        const int u = threadIdx.x - (kFirstConvWarp + team * kTeamWarps) * 32;   // 0..255
+        const int c = u & 7, q = u >> 3;                                         // q 0..31
+        uint32_t g0 = 0;                        // global index of the item's first stage
         int local = 0;
         bool ok = true;
         for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
             const Item it = decode_item(p, item);
             const int n_stages = p.a[it.a].n_stages;
             const bool diag = it.diag;
-            // per-input code sums: byte lanes (<= 16 rows), then 16-bit lanes
-            uint32_t b8[2][2][4], s16lo[2][2][4], s16hi[2][2][4];
+            const bool tile_j = diag || q < 16;
+            const int n_units = diag ? 2 : 4;
+            const int row0 = diag ? q : (q & 15), row_step = diag ? 32 : 16;
+            const uint32_t src_tile = tile_j ? uint32_t(kPackedTileBytes) : 0u;
+            // per-input code sums of this thread's 16 inputs: byte lanes
+            // (<= 16 rows of codes <= 15 between widenings), then 16-bit lanes
+            uint32_t b8[2][4], s16lo[2][4], s16hi[2][4];
 #pragma unroll
-            for (int t = 0; t < 2; ++t)
+            for (int m = 0; m < 2; ++m)
 #pragma unroll
-                for (int q = 0; q < 2; ++q)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) b8[t][q][k] = s16lo[t][q][k] = s16hi[t][q][k] = 0;
-            for (int s = 0; s < n_stages; ++s) {
+                for (int k = 0; k < 4; ++k) b8[m][k] = s16lo[m][k] = s16hi[m][k] = 0;
+            int since_widen = 0;
+            const uint32_t first = g0 + uint32_t((team - int(g0 & 1u)) & 1);
+            for (uint32_t gg = first; gg < g0 + uint32_t(n_stages); gg += 2) {
+                const int pstage = int(gg % kPackedStages), cstage = int(gg % kPlaneStages);
+                const uint32_t pphase = (gg / kPackedStages) & 1u, cphase = (gg / kPlaneStages) & 1u;
                 if (!mbar_wait(bar_packed_full(pstage), pphase, abort, p.status, 4, p.wait_limit) ||
                     !mbar_wait(bar_plane_empty(cstage), cphase ^ 1u, abort, p.status, 5, p.wait_limit)) {
                     ok = false;
                     break;
                 }
-                const uint8_t *pk = smem + kSmPacked + pstage * kPackedStageBytes;
+                const uint8_t *pk = smem + kSmPacked + pstage * kPackedStageBytes + src_tile;
                 uint8_t *pl = smem + kSmPlanes + cstage * kPlaneStageBytes;
-                const uint4 wj = *reinterpret_cast<const uint4 *>(pk + kPackedTileBytes + po);
-                uint4 wi = make_uint4(0u, 0u, 0u, 0u);
-                if (!diag) wi = *reinterpret_cast<const uint4 *>(pk + po);
-                {
-                    const uint32_t ww[4] = {wj.x, wj.y, wj.z, wj.w};
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    if (k >= n_units) break;
+                    const int row = row0 + k * row_step;
+                    const uint4 w = *reinterpret_cast<const uint4 *>(pk + row * 128 + c * 16);
+                    const uint32_t so = uint32_t(row * 128 + ((c ^ (row & 7)) << 4));
+                    const uint32_t ww[4] = {w.x, w.y, w.z, w.w};
                     uint32_t R[4], M[4];
 #pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        codes(ww[k], kZeroInvalid, R[k], M[k]);
-                        b8[1][0][k] += R[k];
-                        b8[1][1][k] += M[k];
+                    for (int e = 0; e < 4; ++e) {
+                        codes(ww[e], kZeroInvalid, R[e], M[e]);
+                        b8[0][e] += R[e];
+                        b8[1][e] += M[e];
                     }
-                    *reinterpret_cast<uint4 *>(pl + kOffMJ + so) = make_uint4(M[0], M[1], M[2], M[3]);
-                    *reinterpret_cast<uint4 *>(pl + kOffRJ + so) = make_uint4(R[0], R[1], R[2], R[3]);
-                    *reinterpret_cast<uint4 *>(pl + kOffNMJ + so) =
-                        make_uint4(M[0] | 0x80808080u, M[1] | 0x80808080u, M[2] | 0x80808080u,
-                                   M[3] | 0x80808080u);
-                }
-                if (!diag) {
-                    const uint32_t ww[4] = {wi.x, wi.y, wi.z, wi.w};
-                    uint32_t R[4], M[4];
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        codes(ww[k], kZeroInvalid, R[k], M[k]);
-                        b8[0][0][k] += R[k];
-                        b8[0][1][k] += M[k];
+                    if (tile_j) {
+                        *reinterpret_cast<uint4 *>(pl + kOffMJ + so) = make_uint4(M[0], M[1], M[2], M[3]);
+                        *reinterpret_cast<uint4 *>(pl + kOffRJ + so) = make_uint4(R[0], R[1], R[2], R[3]);
+                        *reinterpret_cast<uint4 *>(pl + kOffNMJ + so) =
+                            make_uint4(M[0] | 0x80808080u, M[1] | 0x80808080u, M[2] | 0x80808080u,
+                                       M[3] | 0x80808080u);
+                    } else {
+                        *reinterpret_cast<uint4 *>(pl + kOffRI + so) = make_uint4(R[0], R[1], R[2], R[3]);
+                        *reinterpret_cast<uint4 *>(pl + kOffMI + so) = make_uint4(M[0], M[1], M[2], M[3]);
                     }
-                    *reinterpret_cast<uint4 *>(pl + kOffRI + so) = make_uint4(R[0], R[1], R[2], R[3]);
-                    *reinterpret_cast<uint4 *>(pl + kOffMI + so) = make_uint4(M[0], M[1], M[2], M[3]);
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
                 __syncwarp();
@@ -542,65 +559,57 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                     mbar_arrive(bar_plane_full(cstage));
                     mbar_arrive(bar_packed_empty(pstage));
                 }
-                if (++pstage == kPackedStages) {
-                    pstage = 0;
-                    pphase ^= 1u;
-                }
-                if (++cstage == kPlaneStages) {
-                    cstage = 0;
-                    cphase ^= 1u;
-                }
-                // byte lanes hold at most 16 rows of codes <= 15 (240): widen every 16 stages
-                if ((s & 15) == 15 || s + 1 == n_stages) {
+                // byte lanes: at most 4 stages x 4 rows of codes <= 15 (240)
+                if (++since_widen == 4) {
+                    since_widen = 0;
 #pragma unroll
-                    for (int t = 0; t < 2; ++t)
+                    for (int m = 0; m < 2; ++m)
 #pragma unroll
-                        for (int q = 0; q < 2; ++q)
-#pragma unroll
-                            for (int k = 0; k < 4; ++k) {
-                                s16lo[t][q][k] += b8[t][q][k] & 0x00FF00FFu;
-                                s16hi[t][q][k] += (b8[t][q][k] >> 8) & 0x00FF00FFu;
-                                b8[t][q][k] = 0;
-                            }
+                        for (int k = 0; k < 4; ++k) {
+                            s16lo[m][k] += b8[m][k] & 0x00FF00FFu;
+                            s16hi[m][k] += (b8[m][k] >> 8) & 0x00FF00FFu;
+                            b8[m][k] = 0;
+                        }
                 }
             }
             if (!ok) break;
+            g0 += uint32_t(n_stages);
+#pragma unroll
+            for (int m = 0; m < 2; ++m)
+#pragma unroll
+                for (int k = 0; k < 4; ++k) {
+                    s16lo[m][k] += b8[m][k] & 0x00FF00FFu;
+                    s16hi[m][k] += (b8[m][k] >> 8) & 0x00FF00FFu;
+                }
             // reduce over the four lanes of this warp that share chunk column c
-            // (16-bit lanes stay below 4 x 512 x 15 < 2^16), then hand the
-            // per-input sums of this item to the epilogue
+            // and tile (16-bit lanes stay below 4 x 256 x 4 x 15 < 2^16), then
+            // hand the per-input sums of this item to the epilogue
 #pragma unroll
-            for (int t = 0; t < 2; ++t)
+            for (int m = 0; m < 2; ++m)
 #pragma unroll
-                for (int q = 0; q < 2; ++q)
-#pragma unroll
-                    for (int k = 0; k < 4; ++k) {
-                        s16lo[t][q][k] += __shfl_xor_sync(0xFFFFFFFFu, s16lo[t][q][k], 8);
-                        s16lo[t][q][k] += __shfl_xor_sync(0xFFFFFFFFu, s16lo[t][q][k], 16);
-                        s16hi[t][q][k] += __shfl_xor_sync(0xFFFFFFFFu, s16hi[t][q][k], 8);
-                        s16hi[t][q][k] += __shfl_xor_sync(0xFFFFFFFFu, s16hi[t][q][k], 16);
-                    }
+                for (int k = 0; k < 4; ++k) {
+                    s16lo[m][k] += __shfl_xor_sync(0xFFFFFFFFu, s16lo[m][k], 8);
+                    s16lo[m][k] += __shfl_xor_sync(0xFFFFFFFFu, s16lo[m][k], 16);
+                    s16hi[m][k] += __shfl_xor_sync(0xFFFFFFFFu, s16hi[m][k], 8);
+                    s16hi[m][k] += __shfl_xor_sync(0xFFFFFFFFu, s16hi[m][k], 16);
+                }
             const int buf = local & 1;
-            if (!warp_wait(bar_sums_empty(buf), ((sphase >> buf) & 1u) ^ 1u, abort, p.status, 6, lane, p.wait_limit, 64)) {
+            if (!warp_wait(bar_sums_empty(buf), ((local >> 1) & 1) ^ 1, abort, p.status, 6, lane, p.wait_limit, 64)) {
                 ok = false;
                 break;
             }
-            sphase ^= 1u << buf;
             if (lane < 8) {
-                int *sb = sums + buf * (2 * 2 * kTile);
+                int *sb = sums + buf * (2 * 2 * kTile) + (tile_j ? 1 : 0) * 2 * kTile;
 #pragma unroll
-                for (int t = 0; t < 2; ++t) {
-                    if (t == 0 && diag) continue;
+                for (int m = 0; m < 2; ++m) {
+                    int *row_sums = sb + m * kTile;
 #pragma unroll
-                    for (int q = 0; q < 2; ++q) {
-                        int *row_sums = sb + (t * 2 + q) * kTile;
-#pragma unroll
-                        for (int k = 0; k < 4; ++k) {
-                            const int n0 = c * 16 + 4 * k;
-                            atomicAdd(row_sums + sum_slot(n0 + 0), int(s16lo[t][q][k] & 0xFFFFu));
-                            atomicAdd(row_sums + sum_slot(n0 + 1), int(s16hi[t][q][k] & 0xFFFFu));
-                            atomicAdd(row_sums + sum_slot(n0 + 2), int(s16lo[t][q][k] >> 16));
-                            atomicAdd(row_sums + sum_slot(n0 + 3), int(s16hi[t][q][k] >> 16));
-                        }
+                    for (int k = 0; k < 4; ++k) {
+                        const int n0 = c * 16 + 4 * k;
+                        atomicAdd(row_sums + sum_slot(n0 + 0), int(s16lo[m][k] & 0xFFFFu));
+                        atomicAdd(row_sums + sum_slot(n0 + 1), int(s16hi[m][k] & 0xFFFFu));
+                        atomicAdd(row_sums + sum_slot(n0 + 2), int(s16lo[m][k] >> 16));
+                        atomicAdd(row_sums + sum_slot(n0 + 3), int(s16hi[m][k] >> 16));
                     }
                 }
             }
