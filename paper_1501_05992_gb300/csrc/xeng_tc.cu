@@ -435,6 +435,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
     } else if (warp == 1) {
         // ---------------------------------------------------- MMA issuer --
         if (lane == 0) {
+            const uint64_t desc_planes = smem_desc(sbase + kSmPlanes, kPlaneBytes, 1024);
             int stage = 0;
             uint32_t phase = 0;
             uint32_t acc_phase = 0;                  // bit b: phase of accumulator buffer b
@@ -452,6 +453,12 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 acc_phase ^= 1u << buf;
                 fence_after();
                 const uint32_t d_tmem = tmem + uint32_t(buf * 256);
+                // descriptors differ only in the start-address field (bits 0-13,
+                // address >> 4, below 2^14 for any shared address): build the
+                // plane-stage-0 descriptors once and add offsets
+                const uint64_t dR = desc_planes + uint64_t((diag ? kOffRJ : kOffRI) >> 4);
+                const uint64_t dM = desc_planes + uint64_t((diag ? kOffMJ : kOffMI) >> 4);
+                const uint64_t dRJ = desc_planes + uint64_t(kOffRJ >> 4), dMJ = desc_planes + uint64_t(kOffMJ >> 4);
                 uint32_t accum = 0;
                 for (int s = 0; s < n_stages; ++s) {
                     if (!mbar_wait(bar_plane_full(stage), phase, abort, p.status, 3, p.wait_limit)) {
@@ -459,18 +466,12 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                         break;
                     }
                     fence_after();
-                    const uint32_t ps = sbase + kSmPlanes + stage * kPlaneStageBytes;
-                    const uint32_t aR = ps + (diag ? kOffRJ : kOffRI);
-                    const uint32_t aM = ps + (diag ? kOffMJ : kOffMI);
-#pragma unroll
-                    for (int ks = 0; ks < kTc / 32; ++ks) {
-                        const uint32_t ko = uint32_t(ks) * 4096u;
-                        mma_f8(d_tmem, smem_desc(aR + ko, kPlaneBytes, 1024),
-                               smem_desc(ps + kOffRJ + ko, kPlaneBytes, 1024), accum);
-                        accum = 1;
-                        mma_f8(d_tmem, smem_desc(aM + ko, kPlaneBytes, 1024),
-                               smem_desc(ps + kOffMJ + ko, kPlaneBytes, 1024), 1);
-                    }
+                    const uint64_t so = uint64_t((stage * kPlaneStageBytes) >> 4);
+                    mma_f8(d_tmem, dR + so, dRJ + so, accum);
+                    mma_f8(d_tmem, dM + so, dMJ + so, 1);
+                    mma_f8(d_tmem, dR + so + 256u, dRJ + so + 256u, 1);
+                    mma_f8(d_tmem, dM + so + 256u, dMJ + so + 256u, 1);
+                    accum = 1;
                     mma_commit(bar_plane_empty(stage));
                     if (++stage == kPlaneStages) {
                         stage = 0;
