@@ -4,9 +4,12 @@
 Workload (default "full_band"): 256 inputs x 3072 fine channels, 16
 consecutive integrations of 5000 samples (0.5 s at 10 kHz), 4+4-bit voltages
 from the seeded gauss3 recipe, generated in device memory before timing.  One
-step = 16 x (corr_accumulate of one integration + corr_dump of its packed
-triangle): the whole hot path over 8 s of data (62.9 GB of voltages, larger
-than L2, so no flush is needed between steps).
+step = 16 whole integrations, each unpacked, correlated and written out as its
+packed triangle: the whole hot path over 8 s of data (62.9 GB of voltages,
+larger than L2, so no flush is needed between steps).  Graph mode (default)
+replays one captured corr_batch_integrate per integration (the X-engine
+epilogue stores the triangle straight into the output); direct mode issues
+corr_batch_accumulate + corr_batch_dump per integration.
 
 Prints one JSON line (rank 0).  `value` is device-resident throughput, `e2e`
 the same metric through the host-buffer C-ABI calls (host->device copies of
@@ -319,10 +322,11 @@ def run_ours(args, world, rank, local):
         return [v[k * t:(k + 1) * t] for v, (n, f, t) in zip(volts, arrays)]
 
     # kernel timing: the library profiler brackets every X-engine and dump
-    # launch with CUDA events on the launch stream (direct mode); in graph mode
-    # the bench brackets every graph launch (= X-engine + dump of one
-    # integration) with its own events on the same stream, and the dump's
-    # share comes from a short profiled direct pass after the timed region
+    # launch with CUDA events on the launch stream (direct mode: accumulate +
+    # dump per integration); in graph mode each integration is one captured
+    # corr_batch_integrate (the X-engine epilogue writes the triangle straight
+    # into the output, no dump pass), and the bench brackets every graph launch
+    # with its own events on the same stream
     graphs = []
     if args.mode == "graph":
         for k in range(n_int):
@@ -381,24 +385,26 @@ def run_ours(args, world, rank, local):
         kernel_ms = {k: sum(p[k]["ms"] for p in prof) / args.steps for k in prof[0]}
         timing_note = "library CUDA events around every X-engine launch in the timed region"
     else:
-        # dump share from one profiled direct integration after the timed region
+        # launch counts and the X-engine's share of a graph (other kernels, such
+        # as the CUDA-core path's unpack, run inside it too) from one profiled
+        # direct integration after the timed region
         batch.profile_enable(True)
         with torch.cuda.stream(stream):
-            batch.accumulate(integration(0), stream=stream)
-            batch.dump(outs[0], stream=stream)
+            batch.integrate(integration(0), outs[0], stream=stream)
         stream.synchronize()
         prof = batch.profile_read(reset=True)
         batch.profile_enable(False)
         per_int_launches = sum(p[k]["launches"] for p in prof for k in p)
         launches_per_step = per_int_launches * n_int
-        dump_ms = sum(p["dump"]["ms"] for p in prof)
+        all_ms = sum(p[k]["ms"] for p in prof for k in p)
+        xe_share = sum(p["xengine"]["ms"] for p in prof) / all_ms if all_ms > 0 else 1.0
         g_ms = [a.elapsed_time(b) for a, b in gev]
-        xe_ms = sum(max(0.0, m - dump_ms) for m in g_ms)
+        xe_ms = sum(g_ms) * xe_share
         xe_timed = len(g_ms) * max(1, sum(p["xengine"]["launches"] for p in prof))
-        kernel_ms = {"graph_per_integration": sum(g_ms) / len(g_ms), "dump": dump_ms,
-                     "xengine_per_integration": xe_ms / len(g_ms)}
-        timing_note = ("CUDA events around every graph launch of the last timed step, "
-                       "minus the dump time of a profiled direct integration")
+        kernel_ms = {"graph_per_integration": sum(g_ms) / len(g_ms),
+                     "xengine_per_integration": xe_ms / len(g_ms), "xengine_share": xe_share}
+        timing_note = ("CUDA events around every graph launch (one integration each) of the last "
+                       "timed step, times the X-engine's share of a profiled direct integration")
     xe_per_step = xe_timed if args.mode == "graph" else xe_timed // max(1, args.steps)
     peaks, src = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count

@@ -150,6 +150,18 @@ int corr_dump(corr_ctx *ctx, int32_t *d_vis, void *stream);
 long long corr_samples(const corr_ctx *ctx);
 
 /*
+ * One whole integration in one call: correlate n_time samples of d_volt
+ * (device, [n_time][n_chan][n_inputs]) and write their packed triangle to
+ * d_vis (device int32 [n_chan][P][2]), as corr_accumulate on an empty
+ * integration followed by corr_dump would, but with the X-engine epilogue
+ * storing straight into d_vis (Section 3.4.3: the products of one
+ * integration are written out once) -- no accumulator pass and no copy.
+ * The context's running integration and accumulators are not touched.
+ * n_time 0 writes zeros; n_time above n_time_per_int is CORR_E_OVERFLOW.
+ */
+int corr_integrate(corr_ctx *ctx, const uint8_t *d_volt, int n_time, int32_t *d_vis, void *stream);
+
+/*
  * End-to-end variants over HOST buffers: h_volt is host memory
  * [n_time][n_chan][n_inputs] (pinned memory gives full copy bandwidth); the
  * library copies it in chunks of up to 500 samples through a ring of three
@@ -272,16 +284,25 @@ int corr_batch_accumulate(corr_batch *b, const uint8_t *const *d_volt, const int
 /* Dump every array a with d_vis[a] != NULL (device int32 [F_a][P_a][2]). */
 int corr_batch_dump(corr_batch *b, int32_t *const *d_vis, void *stream);
 
+/*
+ * corr_integrate for every array a with d_vis[a] != NULL, the tensor-core
+ * arrays sharing one persistent launch: array a's n_time[a] samples of
+ * d_volt[a] become the triangle in d_vis[a].  Running integrations are not
+ * touched.  All checks happen before anything is enqueued.
+ */
+int corr_batch_integrate(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
+                         int32_t *const *d_vis, void *stream);
+
 /* corr_sync for every array of the batch. */
 int corr_batch_sync(corr_batch *b, void *stream);
 
 /*
- * Capture one whole integration -- corr_batch_accumulate(d_volt, n_time)
- * followed by corr_batch_dump(d_vis) -- into an executable CUDA graph
- * (returned as an opaque handle in *graph_exec).  The batch must be between
- * integrations (every array at 0 samples, else CORR_E_STATE) and stays so:
- * each corr_graph_launch replays the full integration on the captured
- * buffers.  `stream` must not be the legacy default stream (CORR_E_ARG).
+ * Capture one whole integration -- corr_batch_integrate(d_volt, n_time,
+ * d_vis) -- into an executable CUDA graph (returned as an opaque handle in
+ * *graph_exec).  Each corr_graph_launch replays it on the captured buffers:
+ * whatever d_volt holds then becomes the triangles in d_vis.  The batch's
+ * running integrations are not involved.  `stream` must not be the legacy
+ * default stream (CORR_E_ARG).
  * Profiling events recorded during capture become graph nodes; launches that
  * cannot be timed from them are left out of corr_profile_read's "timed" and
  * "ms" (launch counts cover the capture only).

@@ -101,6 +101,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_accumulate": ([vp, vp, c_int, vp], c_int),
             "corr_dump": ([vp, vp, vp], c_int),
             "corr_samples": ([vp], ctypes.c_longlong),
+            "corr_integrate": ([vp, vp, c_int, vp, vp], c_int),
             "corr_accumulate_host": ([vp, vp, c_int, vp], c_int),
             "corr_dump_host": ([vp, vp, vp], c_int),
             "corr_sync": ([vp, vp], c_int),
@@ -118,6 +119,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_batch_array": ([vp, c_int], vp),
             "corr_batch_accumulate": ([vp, ctypes.POINTER(vp), ctypes.POINTER(c_int), vp], c_int),
             "corr_batch_dump": ([vp, ctypes.POINTER(vp), vp], c_int),
+            "corr_batch_integrate": ([vp, ctypes.POINTER(vp), ctypes.POINTER(c_int), ctypes.POINTER(vp), vp],
+                                     c_int),
             "corr_batch_sync": ([vp, vp], c_int),
             "corr_batch_graph_capture": ([vp, ctypes.POINTER(vp), ctypes.POINTER(c_int),
                                           ctypes.POINTER(vp), vp, ctypes.POINTER(vp)], c_int),
@@ -259,6 +262,20 @@ class Correlator:
             raise ValueError("out must be a contiguous int32 [F][P][2] tensor on the device")
         _check(self._lib.corr_dump(self._ctx, ctypes.c_void_p(out.data_ptr()),
                                    _stream_handle(stream)), "corr_dump")
+        return out
+
+    def integrate(self, volt: torch.Tensor, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """One whole integration of `volt` written straight to `out` (see corr_integrate);
+        the running integration is not touched."""
+        nt = self._check_volt(volt, device=True)
+        if out is None:
+            out = torch.empty((self.n_chan, self.n_pairs, 2), dtype=torch.int32, device=self.device)
+        elif (out.dtype != torch.int32 or out.shape != (self.n_chan, self.n_pairs, 2)
+              or not out.is_contiguous() or out.device != self.device):
+            raise ValueError("out must be a contiguous int32 [F][P][2] tensor on the device")
+        vptr = ctypes.c_void_p(volt.data_ptr()) if nt > 0 else ctypes.c_void_p(0)
+        _check(self._lib.corr_integrate(self._ctx, vptr, nt, ctypes.c_void_p(out.data_ptr()),
+                                        _stream_handle(stream)), "corr_integrate")
         return out
 
     def accumulate_host(self, volt: torch.Tensor, stream=None) -> None:
@@ -448,11 +465,19 @@ class Batch:
                "corr_batch_dump")
         return outs
 
+    def integrate(self, volts, outs=None, stream=None):
+        """Whole integrations of every array straight into `outs` (see corr_batch_integrate)."""
+        ptrs, nt = self._volts(volts)
+        outs = self._outs(outs)
+        _check(self._lib.corr_batch_integrate(self._h, ptrs, nt, self._ptrs(outs, "vis"),
+                                              _stream_handle(stream)), "corr_batch_integrate")
+        return outs
+
     def sync(self, stream=None) -> None:
         _check(self._lib.corr_batch_sync(self._h, _stream_handle(stream)), "corr_batch_sync")
 
     def capture(self, volts, outs=None, stream=None) -> tuple[Graph, list]:
-        """Capture accumulate(volts) + dump(outs) as one replayable graph."""
+        """Capture integrate(volts, outs) as one replayable graph."""
         if stream is None:
             stream = torch.cuda.Stream(self.device)
         ptrs, nt = self._volts(volts)

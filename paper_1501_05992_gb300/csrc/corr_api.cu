@@ -162,13 +162,13 @@ int wait_host_dump(corr_ctx *c, cudaStream_t s)
     return CORR_OK;
 }
 
-// Correlate n_time samples already in device memory.
-int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
+// Correlate n_time samples already in device memory into the packed triangle
+// `target` (the context's accumulators, or a caller's output buffer for a
+// whole integration); fresh: the first launch stores instead of adding.
+int accumulate_to(corr_ctx *c, const uint8_t *volt, int nt, int32_t *target, bool fresh, cudaStream_t s)
 {
-    if (wait_host_dump(c, s) != CORR_OK) return CORR_E_CUDA;
     const int path = resolve_path(c, c->path);
     const bool zi = (c->flags & CORR_ZERO_INVALID) != 0;
-    bool fresh = c->fresh;
     cudaError_t e = cudaSuccess;
     const size_t row = size_t(c->f) * size_t(c->n);
     if (path == CORR_PATH_TC_FP8) {
@@ -179,7 +179,7 @@ int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
             opt.wait_limit = c->wait_limit;
             opt.inject_stall = c->inject_stall;
             c->inject_stall = false;
-            e = launch_xeng_tc(volt + size_t(t0) * row, c->f, c->n, ntc, zi, c->acc, fresh,
+            e = launch_xeng_tc(volt + size_t(t0) * row, c->f, c->n, ntc, zi, target, fresh,
                                c->status, opt, s);
             prof_end(c, CORR_K_XENGINE, s, 1);
             if (e != cudaSuccess) return cuda_fail(e);
@@ -203,7 +203,7 @@ int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
                 prof_end(c, CORR_K_UNPACK, s, 1);
                 if (e != cudaSuccess) return cuda_fail(e);
                 prof_begin(c, s);
-                e = launch_xeng_dp4a(A, W, c->n, n_pad, fc, tw_pad, c->acc, f0, fresh, tile, s);
+                e = launch_xeng_dp4a(A, W, c->n, n_pad, fc, tw_pad, target, f0, fresh, tile, s);
                 prof_end(c, CORR_K_XENGINE, s, 1);
                 if (e != cudaSuccess) return cuda_fail(e);
             }
@@ -225,7 +225,7 @@ int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
                 prof_end(c, CORR_K_UNPACK, s, 1);
                 if (e != cudaSuccess) return cuda_fail(e);
                 prof_begin(c, s);
-                e = launch_xeng_mma8(X, Xt, c->n, P.n_pad, fc, t_pad, c->acc, f0, fresh, s);
+                e = launch_xeng_mma8(X, Xt, c->n, P.n_pad, fc, t_pad, target, f0, fresh, s);
                 prof_end(c, CORR_K_XENGINE, s, 1);
                 if (e != cudaSuccess) return cuda_fail(e);
             }
@@ -234,6 +234,15 @@ int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
     } else {
         return CORR_E_UNSUPPORTED;
     }
+    return CORR_OK;
+}
+
+// Add n_time samples to the running integration.
+int accumulate_device(corr_ctx *c, const uint8_t *volt, int nt, cudaStream_t s)
+{
+    if (wait_host_dump(c, s) != CORR_OK) return CORR_E_CUDA;
+    const int rc = accumulate_to(c, volt, nt, c->acc, c->fresh, s);
+    if (rc != CORR_OK) return rc;
     c->fresh = false;
     return CORR_OK;
 }
@@ -481,6 +490,23 @@ int corr_dump(corr_ctx *c, int32_t *d_vis, void *stream)
     c->fresh = true;
     c->samples = 0;
     return ret(CORR_OK);
+}
+
+int corr_integrate(corr_ctx *c, const uint8_t *d_volt, int n_time, int32_t *d_vis, void *stream)
+{
+    if (!c || n_time < 0 || !d_vis) return ret(CORR_E_ARG);
+    if (!c->ws) return ret(CORR_E_STATE);
+    if (n_time > c->t_max) return ret(CORR_E_OVERFLOW);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n_time == 0) {
+        if (cudaMemsetAsync(d_vis, 0, acc_words(c) * sizeof(int32_t), s) != cudaSuccess) {
+            cudaGetLastError();
+            return ret(CORR_E_CUDA);
+        }
+        return ret(CORR_OK);
+    }
+    if (!d_volt) return ret(CORR_E_ARG);
+    return ret(accumulate_to(c, d_volt, n_time, d_vis, true, s));
 }
 
 long long corr_samples(const corr_ctx *c)
@@ -760,23 +786,20 @@ corr_ctx *corr_batch_array(corr_batch *b, int a)
     return b->ctx[a];
 }
 
-int corr_batch_accumulate(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
-                          void *stream)
+namespace {
+
+// Correlate every array of a batch that has data: tensor-core arrays in one
+// persistent launch per group of up to CORR_BATCH_TC_GROUP arrays and per
+// kTcMaxSamples samples, the others on their own kernels.  With `into` null
+// the samples are added to the arrays' running integrations; otherwise each
+// array's whole integration is written to into[a] (its accumulators are left
+// alone).
+int batch_correlate(corr_batch *b, const uint8_t *const *d_volt, const int *n_time, int32_t *const *into,
+                    cudaStream_t s)
 {
-    if (!b || !d_volt || !n_time) return ret(CORR_E_ARG);
-    if (!b->bound) return ret(CORR_E_STATE);
-    // every check before anything is enqueued
-    for (int a = 0; a < b->n; ++a) {
-        if (n_time[a] < 0) return ret(CORR_E_ARG);
-        if (!d_volt[a] || n_time[a] == 0) continue;
-        if (b->ctx[a]->samples + n_time[a] > b->ctx[a]->t_max) return ret(CORR_E_OVERFLOW);
-    }
-    cudaStream_t s = static_cast<cudaStream_t>(stream);
-    // tensor-core arrays: one persistent launch per group of up to
-    // CORR_BATCH_TC_GROUP arrays and per kTcMaxSamples samples
     int tc[CORR_BATCH_MAX], n_tc = 0, max_nt = 0;
     for (int a = 0; a < b->n; ++a) {
-        if (!d_volt[a] || n_time[a] == 0) continue;
+        if (!d_volt[a] || n_time[a] == 0 || (into && !into[a])) continue;
         if (resolve_path(b->ctx[a], b->ctx[a]->path) == CORR_PATH_TC_FP8) {
             tc[n_tc++] = a;
             if (n_time[a] > max_nt) max_nt = n_time[a];
@@ -789,16 +812,17 @@ int corr_batch_accumulate(corr_batch *b, const uint8_t *const *d_volt, const int
             TcArray arr[CORR_BATCH_TC_GROUP];
             int k = 0;
             for (int x = 0; x < gn; ++x) {
-                corr_ctx *c = b->ctx[tc[g0 + x]];
-                const int nt = n_time[tc[g0 + x]];
+                const int a = tc[g0 + x];
+                corr_ctx *c = b->ctx[a];
+                const int nt = n_time[a];
                 const int ntc = nt - t0 <= 0 ? 0 : (nt - t0 < kTcMaxSamples ? nt - t0 : kTcMaxSamples);
-                arr[k].volt = d_volt[tc[g0 + x]] + size_t(t0 > nt ? nt : t0) * size_t(c->f) * size_t(c->n);
-                arr[k].acc = c->acc;
+                arr[k].volt = d_volt[a] + size_t(t0 > nt ? nt : t0) * size_t(c->f) * size_t(c->n);
+                arr[k].acc = into ? into[a] : c->acc;
                 arr[k].n_chan = c->f;
                 arr[k].n = c->n;
                 arr[k].nt = ntc;
                 arr[k].zero_invalid = (c->flags & CORR_ZERO_INVALID) != 0;
-                arr[k].fresh = t0 == 0 ? c->fresh : false;
+                arr[k].fresh = t0 == 0 ? (into ? true : c->fresh) : false;
                 ++k;
             }
             TcOptions opt;
@@ -808,23 +832,67 @@ int corr_batch_accumulate(corr_batch *b, const uint8_t *const *d_volt, const int
             prof_begin(lead, s);
             cudaError_t e = launch_xeng_tc_batch(arr, k, lead->status, opt, s);
             prof_end(lead, CORR_K_XENGINE, s, 1);
-            if (e != cudaSuccess) return ret(cuda_fail(e));
+            if (e != cudaSuccess) return cuda_fail(e);
         }
-        for (int x = 0; x < gn; ++x) {
-            corr_ctx *c = b->ctx[tc[g0 + x]];
-            c->fresh = false;
-            c->samples += n_time[tc[g0 + x]];
+        if (!into) {
+            for (int x = 0; x < gn; ++x) {
+                corr_ctx *c = b->ctx[tc[g0 + x]];
+                c->fresh = false;
+                c->samples += n_time[tc[g0 + x]];
+            }
         }
     }
-    // every other array on its own kernels
     for (int a = 0; a < b->n; ++a) {
-        if (!d_volt[a] || n_time[a] == 0) continue;
+        if (!d_volt[a] || n_time[a] == 0 || (into && !into[a])) continue;
         if (resolve_path(b->ctx[a], b->ctx[a]->path) == CORR_PATH_TC_FP8) continue;
-        const int rc = accumulate_device(b->ctx[a], d_volt[a], n_time[a], s);
-        if (rc != CORR_OK) return ret(rc);
-        b->ctx[a]->samples += n_time[a];
+        if (into) {
+            const int rc = accumulate_to(b->ctx[a], d_volt[a], n_time[a], into[a], true, s);
+            if (rc != CORR_OK) return rc;
+        } else {
+            const int rc = accumulate_device(b->ctx[a], d_volt[a], n_time[a], s);
+            if (rc != CORR_OK) return rc;
+            b->ctx[a]->samples += n_time[a];
+        }
     }
-    return ret(CORR_OK);
+    return CORR_OK;
+}
+
+}  // namespace
+
+int corr_batch_accumulate(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
+                          void *stream)
+{
+    if (!b || !d_volt || !n_time) return ret(CORR_E_ARG);
+    if (!b->bound) return ret(CORR_E_STATE);
+    // every check before anything is enqueued
+    for (int a = 0; a < b->n; ++a) {
+        if (n_time[a] < 0) return ret(CORR_E_ARG);
+        if (!d_volt[a] || n_time[a] == 0) continue;
+        if (b->ctx[a]->samples + n_time[a] > b->ctx[a]->t_max) return ret(CORR_E_OVERFLOW);
+    }
+    return ret(batch_correlate(b, d_volt, n_time, nullptr, static_cast<cudaStream_t>(stream)));
+}
+
+int corr_batch_integrate(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
+                         int32_t *const *d_vis, void *stream)
+{
+    if (!b || !d_volt || !n_time || !d_vis) return ret(CORR_E_ARG);
+    if (!b->bound) return ret(CORR_E_STATE);
+    for (int a = 0; a < b->n; ++a) {
+        if (n_time[a] < 0) return ret(CORR_E_ARG);
+        if (!d_vis[a]) continue;
+        if (n_time[a] > b->ctx[a]->t_max) return ret(CORR_E_OVERFLOW);
+        if (n_time[a] > 0 && !d_volt[a]) return ret(CORR_E_ARG);
+    }
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    for (int a = 0; a < b->n; ++a) {
+        if (!d_vis[a] || n_time[a] > 0) continue;
+        if (cudaMemsetAsync(d_vis[a], 0, acc_words(b->ctx[a]) * sizeof(int32_t), s) != cudaSuccess) {
+            cudaGetLastError();
+            return ret(CORR_E_CUDA);
+        }
+    }
+    return ret(batch_correlate(b, d_volt, n_time, d_vis, s));
 }
 
 int corr_batch_dump(corr_batch *b, int32_t *const *d_vis, void *stream)
@@ -855,22 +923,17 @@ int corr_batch_graph_capture(corr_batch *b, const uint8_t *const *d_volt, const 
 {
     if (!b || !d_volt || !n_time || !d_vis || !graph_exec || !stream) return ret(CORR_E_ARG);
     if (!b->bound) return ret(CORR_E_STATE);
-    for (int a = 0; a < b->n; ++a)
-        if (b->ctx[a]->samples != 0) return ret(CORR_E_STATE);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     *graph_exec = nullptr;
     if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
         cudaGetLastError();
         return ret(CORR_E_CUDA);
     }
-    int rc = corr_batch_accumulate(b, d_volt, n_time, stream);
-    if (rc == CORR_OK) rc = corr_batch_dump(b, d_vis, stream);
+    // a whole integration straight into the output buffers: the accumulators
+    // are not touched, so replays do not depend on the batch's state
+    int rc = corr_batch_integrate(b, d_volt, n_time, d_vis, stream);
     cudaGraph_t graph = nullptr;
     const cudaError_t e = cudaStreamEndCapture(s, &graph);
-    for (int a = 0; a < b->n; ++a) {
-        b->ctx[a]->samples = 0;       // the captured integration ends with its dump
-        b->ctx[a]->fresh = true;
-    }
     if (rc != CORR_OK || e != cudaSuccess || !graph) {
         cudaGetLastError();
         if (graph) cudaGraphDestroy(graph);

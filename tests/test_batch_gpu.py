@@ -90,6 +90,33 @@ def test_overflow_in_one_array_enqueues_nothing():
     b.sync()
 
 
+def test_batch_integrate_mixed_paths():
+    specs = [{"n_inputs": 128, "n_chan": 6, "n_time_per_int": 900, "path": "auto"},
+             {"n_inputs": 64, "n_chan": 3, "n_time_per_int": 900, "path": "cudacore"},
+             {"n_inputs": 256, "n_chan": 2, "n_time_per_int": 900, "path": "tc_fp8"},
+             {"n_inputs": 40, "n_chan": 4, "n_time_per_int": 900, "path": "mma_i8"}]
+    if not path_available("tc_fp8", 256):
+        specs[2]["path"] = "auto"
+    shapes = [(900, 6, 128), (700, 3, 64), (333, 2, 256), (900, 4, 40)]
+    volts = [_rand(sh, 100 + k) for k, sh in enumerate(shapes)]
+    b = corr.Batch(specs)
+    b.accumulate([torch.from_numpy(volts[0][:100]).cuda(), None, None, None])
+    outs = b.integrate([torch.from_numpy(v).cuda() for v in volts])
+    b.sync()
+    for a in range(4):
+        assert np.array_equal(outs[a].cpu().numpy(), oracle.to_int32(oracle.xmac(volts[a]))), a
+    assert b.samples(0) == 100                       # the running integration is kept
+    part = b.dump()
+    b.sync()
+    assert np.array_equal(part[0].cpu().numpy(), oracle.to_int32(oracle.xmac(volts[0][:100])))
+    # arrays without an output buffer are skipped
+    only1 = torch.full((3, 64 * 65 // 2, 2), -3, dtype=torch.int32, device="cuda")
+    b.integrate([torch.from_numpy(v).cuda() for v in volts], [None, only1, None, None])
+    b.sync()
+    assert np.array_equal(only1.cpu().numpy(), oracle.to_int32(oracle.xmac(volts[1])))
+    b.close()
+
+
 def test_graph_replays_whole_integrations():
     specs = [{"n_inputs": 128, "n_chan": 8, "n_time_per_int": 1000},
              {"n_inputs": 64, "n_chan": 3, "n_time_per_int": 1000, "path": "cudacore"}]

@@ -178,6 +178,47 @@ def test_back_to_back_host_integrations(path):
     c.close()
 
 
+@pytest.mark.parametrize("path", ALL_PATHS)
+def test_integrate_exact_and_leaves_running_integration(path):
+    """corr_integrate writes one whole integration straight to the output and
+    does not disturb an integration that is being accumulated meanwhile."""
+    N, F, T = 128, 5, 1700
+    if not path_available(path, N):
+        pytest.skip(f"{path} unsupported")
+    rng = np.random.default_rng(91)
+    a_np = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    b_np = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    a, b = torch.from_numpy(a_np).cuda(), torch.from_numpy(b_np).cuda()
+    c = corr.Correlator(N, F, T, path=path)
+    c.accumulate(a[:600])
+    got_b = c.integrate(b).cpu().numpy()
+    assert c.samples == 600
+    c.accumulate(a[600:])
+    got_a = c.dump().cpu().numpy()
+    zeros = c.integrate(b[:0]).cpu().numpy()
+    c.sync()
+    assert np.array_equal(got_b, oracle.to_int32(oracle.xmac(b_np)))
+    assert np.array_equal(got_a, oracle.to_int32(oracle.xmac(a_np)))
+    assert not zeros.any()
+    with pytest.raises(corr.CorrError) as e:
+        c.integrate(torch.zeros((T + 1, F, N), dtype=torch.uint8, device="cuda"))
+    assert e.value.status == corr.CORR_E_OVERFLOW
+    c.close()
+
+
+def test_integrate_long_splits_launches():
+    if not path_available("tc_fp8", 128):
+        pytest.skip("tc_fp8 unsupported")
+    N, F, T = 128, 2, 40000
+    volt = np.full((T, F, N), 0x77, np.uint8)
+    volt[::7] = 0x99
+    c = corr.Correlator(N, F, T, path="tc_fp8")
+    got = c.integrate(torch.from_numpy(volt).cuda()).cpu().numpy()
+    c.sync()
+    c.close()
+    assert np.array_equal(got, oracle.to_int32(oracle.xmac(volt)))
+
+
 def test_overflow_and_state_errors():
     c = corr.Correlator(16, 2, 100, path="cudacore")
     v = torch.zeros((60, 2, 16), dtype=torch.uint8, device="cuda")
