@@ -78,6 +78,10 @@ class OracleLib:
         lib.oracle_xmac_pair.restype = c_int
         lib.oracle_decode.argtypes = [u8p, ctypes.c_int64, c_int, i32p, i32p]
         lib.oracle_decode.restype = None
+        lib.oracle_beam.argtypes = [u8p, c_int, c_int, c_int, c_int, c_int, i64p]
+        lib.oracle_beam.restype = c_int
+        lib.oracle_remap.argtypes = [i64p, c_int, c_int, c_int, c_int, i32p, i64p]
+        lib.oracle_remap.restype = c_int
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = c_int
         self.lib = lib
@@ -131,6 +135,34 @@ class OracleLib:
             raise ValueError("oracle_xmac_pair: index out of range")
         return int(out[0]), int(out[1])
 
+    def beam(self, volt: np.ndarray, n_avg: int = 1, zero_invalid: bool = False) -> np.ndarray:
+        """Incoherent beam int64 [T / n_avg][F]: total power of all inputs per channel."""
+        volt = _check_volt(volt)
+        T, F, N = volt.shape
+        out = np.zeros((T // max(n_avg, 1), F), np.int64)
+        if self.lib.oracle_beam(_u8(volt), N, F, T, int(n_avg), int(zero_invalid), _i64(out)) != 0:
+            raise ValueError("oracle_beam: bad arguments")
+        return out
+
+    def remap(self, tri: np.ndarray, nat_of_pfb, f_avg: int = 1) -> np.ndarray:
+        """Station x polarisation products in natural order, int64
+        [F / f_avg][S(S+1)/2][2][2][2], from PFB-order triangles int64
+        [n_dumps][F][P][2] (or one [F][P][2]), summed over the dumps."""
+        t = np.ascontiguousarray(tri, dtype=np.int64)
+        if t.ndim == 3:
+            t = t[None]
+        D, F, P, _ = t.shape
+        N = int(round((np.sqrt(8 * P + 1) - 1) / 2))
+        perm = np.ascontiguousarray(nat_of_pfb, dtype=np.int32)
+        if N * (N + 1) // 2 != P or perm.shape != (N,):
+            raise ValueError("triangle size and permutation length disagree")
+        S = N // 2
+        out = np.zeros((F // max(f_avg, 1), S * (S + 1) // 2, 2, 2, 2), np.int64)
+        i32p = ctypes.POINTER(ctypes.c_int32)
+        if self.lib.oracle_remap(_i64(t), N, F, D, int(f_avg), perm.ctypes.data_as(i32p), _i64(out)) != 0:
+            raise ValueError("oracle_remap: bad arguments")
+        return out
+
     def threads(self) -> int:
         """OpenMP threads the triangle routine uses."""
         return int(self.lib.oracle_threads())
@@ -158,6 +190,24 @@ def xmac_full(volt, zero_invalid=False):
 
 def xmac_pair(volt, f, i, j, zero_invalid=False):
     return default().xmac_pair(volt, f, i, j, zero_invalid)
+
+
+def beam(volt, n_avg=1, zero_invalid=False):
+    return default().beam(volt, n_avg, zero_invalid)
+
+
+def remap(tri, nat_of_pfb, f_avg=1):
+    return default().remap(tri, nat_of_pfb, f_avg)
+
+
+def pfb_order(n_inputs: int) -> np.ndarray:
+    """nat_of_pfb for the PFB input order of Appendix A: within each PFB's 64
+    inputs, position k carries input (k mod 4) * 16 + k div 4 (0, 16, 32, 48,
+    1, 17, ...), and the PFBs' blocks of 64 follow each other (Appendix B)."""
+    if n_inputs % 64 != 0:
+        raise ValueError("the PFB order is defined for whole PFBs of 64 inputs")
+    k = np.arange(n_inputs)
+    return ((k // 64) * 64 + (k % 64 % 4) * 16 + (k % 64) // 4).astype(np.int32)
 
 
 def threads() -> int:

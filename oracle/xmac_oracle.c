@@ -178,6 +178,114 @@ int oracle_xmac_pair(const uint8_t *volt, int N, int F, int T, int zero_invalid,
     return 0;
 }
 
+/*
+ * Incoherent beam (Section 3.4: one of the XMAC's other modes): the total
+ * power of all inputs, per channel and sample, summed over n_avg consecutive
+ * samples:
+ *
+ *     beam[k][f] = sum_{t = k n_avg}^{(k+1) n_avg - 1}  sum_{n < N} |x_n(t,f)|^2
+ *
+ * with |x|^2 = r^2 + m^2 of the decoded sample.  out is int64 [T / n_avg][F];
+ * T must be a multiple of n_avg.  Returns 0, or -1 on bad arguments.
+ */
+int oracle_beam(const uint8_t *volt, int N, int F, int T, int n_avg, int zero_invalid,
+                int64_t *out)
+{
+    if (!volt || !out || N < 1 || F < 1 || T < 0 || n_avg < 1 || T % n_avg != 0)
+        return -1;
+    for (int k = 0; k < T / n_avg; ++k) {
+        for (int f = 0; f < F; ++f) {
+            int64_t p = 0;
+            for (int t = k * n_avg; t < (k + 1) * n_avg; ++t) {
+                const uint8_t *row = volt + ((int64_t)t * F + f) * N;
+                for (int n = 0; n < N; ++n) {
+                    int32_t r, m;
+                    oracle_decode(row + n, 1, zero_invalid, &r, &m);
+                    p += (int64_t)r * r + (int64_t)m * m;
+                }
+            }
+            out[(int64_t)k * F + f] = p;
+        }
+    }
+    return 0;
+}
+
+/*
+ * Output remap (Appendix C, "GPU Output"): the X-engine correlates the inputs
+ * in the order the PFBs deliver them and emits the lower triangle over those
+ * positions; the archived products are per station pair (s1, s2), s2 <= s1,
+ * with the 2 x 2 polarisation products inside, in natural input order, and
+ * a product the triangle holds only as its conjugate has to be conjugated.
+ * Reading taken here: natural input a is station a / 2, polarisation a % 2,
+ * and nat_of_pfb[i] is the natural input at PFB position i.
+ *
+ * Optionally the products are integrated further by f_avg adjacent channels
+ * and over n_dumps consecutive dumps ("integrate by a factor of two in each
+ * dimension", Section 3.4.3):
+ *
+ *     out[g][s1(s1+1)/2 + s2][p1][p2] = sum_{d < n_dumps} sum_{f = g f_avg}^{(g+1) f_avg - 1}
+ *                                      V^{(d)}_{2 s1 + p1, 2 s2 + p2}(f)
+ *
+ * where V_AB = tri[i][j] for i = pos(A) >= j = pos(B) and conj(tri[j][i])
+ * otherwise.  tri is int64 [n_dumps][F][N(N+1)/2][2] (PFB-order triangles),
+ * out int64 [F / f_avg][S(S+1)/2][2][2][2] with S = N / 2.  Returns 0, or -1
+ * on bad arguments (odd N, F not a multiple of f_avg, not a permutation).
+ */
+int oracle_remap(const int64_t *tri, int N, int F, int n_dumps, int f_avg, const int32_t *nat_of_pfb,
+                 int64_t *out)
+{
+    if (!tri || !out || !nat_of_pfb || N < 2 || N % 2 != 0 || F < 1 || n_dumps < 1 || f_avg < 1 ||
+        F % f_avg != 0)
+        return -1;
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)N);
+    if (!pos)
+        return -1;
+    for (int a = 0; a < N; ++a)
+        pos[a] = -1;
+    for (int i = 0; i < N; ++i) {
+        int a = nat_of_pfb[i];
+        if (a < 0 || a >= N || pos[a] != -1) {
+            free(pos);
+            return -1;
+        }
+        pos[a] = i;
+    }
+    const int S = N / 2;
+    const int64_t P = (int64_t)N * (N + 1) / 2;
+    const int64_t Q = (int64_t)S * (S + 1) / 2;
+    for (int g = 0; g < F / f_avg; ++g) {
+        for (int s1 = 0; s1 < S; ++s1) {
+            for (int s2 = 0; s2 <= s1; ++s2) {
+                for (int p1 = 0; p1 < 2; ++p1) {
+                    for (int p2 = 0; p2 < 2; ++p2) {
+                        const int i = pos[2 * s1 + p1], j = pos[2 * s2 + p2];
+                        int64_t re = 0, im = 0;
+                        for (int d = 0; d < n_dumps; ++d) {
+                            for (int f = g * f_avg; f < (g + 1) * f_avg; ++f) {
+                                const int64_t *vf = tri + ((int64_t)d * F + f) * P * 2;
+                                if (i >= j) {
+                                    const int64_t k = (int64_t)i * (i + 1) / 2 + j;
+                                    re += vf[2 * k];
+                                    im += vf[2 * k + 1];
+                                } else {
+                                    const int64_t k = (int64_t)j * (j + 1) / 2 + i;
+                                    re += vf[2 * k];
+                                    im -= vf[2 * k + 1];
+                                }
+                            }
+                        }
+                        int64_t *o = out + (((int64_t)g * Q + (int64_t)s1 * (s1 + 1) / 2 + s2) * 4 + p1 * 2 + p2) * 2;
+                        o[0] = re;
+                        o[1] = im;
+                    }
+                }
+            }
+        }
+    }
+    free(pos);
+    return 0;
+}
+
 /* Number of OpenMP threads the triangle routine would use (1 without OpenMP). */
 int oracle_threads(void)
 {

@@ -252,6 +252,82 @@ def pin_brute_force(o):
                 assert (int(got[0]), int(got[1])) == (int(s.real), int(s.imag))
 
 
+def pin_beam_autos(o):
+    """Summed over time, the incoherent beam is the sum of the autocorrelations
+    (the triangle's diagonal), for both readings of the invalid code."""
+    rng = _rng(23)
+    volt = rng.integers(0, 256, (12, 3, 7), dtype=np.uint8)
+    volt[3, 1, 2] = 0x88
+    for zi in (False, True):
+        beam = o.beam(volt, 1, zi)
+        tri = o.xmac(volt, zi)
+        autos = np.stack([tri[:, tri_index(n, n), 0] for n in range(7)], axis=1).sum(axis=1)
+        assert np.array_equal(beam.sum(axis=0), autos)
+        assert np.array_equal(o.beam(volt, 12, zi)[0], autos)
+        assert np.all(beam >= 0)
+
+
+def pin_beam_brute_force(o):
+    rng = _rng(29)
+    volt = rng.integers(0, 256, (6, 2, 5), dtype=np.uint8)
+    x = numpy_decode(volt)
+    want = (np.abs(x.real) ** 2 + np.abs(x.imag) ** 2).sum(axis=2)        # [T][F], exact in float64
+    want = want.reshape(2, 3, 2).sum(axis=1)                              # n_avg = 3
+    assert np.array_equal(o.beam(volt, 3), want.astype(np.int64))
+
+
+def pin_pfb_order_printed(o):
+    order = __import__("oracle").pfb_order(128)
+    for k, a in read_table("pfb_antenna_order.txt"):
+        assert order[int(k)] == int(a) and order[64 + int(k)] == 64 + int(a)
+    assert sorted(order.tolist()) == list(range(128))
+
+
+def _natural_products(x_nat):
+    """V_AB(f) for every natural pair by numpy's complex matrix product."""
+    T, F, N = x_nat.shape
+    out = np.zeros((F, N, N), np.complex128)
+    for f in range(F):
+        X = x_nat[:, f, :].T                                             # N x T
+        out[f] = X @ X.conj().T
+    return out
+
+
+def pin_remap_natural_order(o):
+    """Correlating in PFB order and remapping equals correlating in natural
+    order (numpy), station pair by station pair, conjugates included; also
+    after averaging over channel pairs and over two dumps."""
+    rng = _rng(31)
+    N, F, T = 8, 4, 10
+    x_nat = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    perm = rng.permutation(N).astype(np.int32)                # nat_of_pfb
+    x_pfb = x_nat[:, :, perm]
+    full = _natural_products(numpy_decode(x_nat))
+    S = N // 2
+    out = o.remap(o.xmac(x_pfb), perm)
+    out2 = o.remap(np.stack([o.xmac(x_pfb[:4]), o.xmac(x_pfb[4:])]), perm, f_avg=2)
+    for s1 in range(S):
+        for s2 in range(s1 + 1):
+            for p1 in range(2):
+                for p2 in range(2):
+                    q = s1 * (s1 + 1) // 2 + s2
+                    v = full[:, 2 * s1 + p1, 2 * s2 + p2]
+                    assert np.array_equal(out[:, q, p1, p2, 0], v.real.astype(np.int64))
+                    assert np.array_equal(out[:, q, p1, p2, 1], v.imag.astype(np.int64))
+                    w = v.reshape(F // 2, 2).sum(axis=1)
+                    assert np.array_equal(out2[:, q, p1, p2, 0], w.real.astype(np.int64))
+                    assert np.array_equal(out2[:, q, p1, p2, 1], w.imag.astype(np.int64))
+
+
+def pin_remap_paper_count(o):
+    d = {k: float(v) for k, v in read_table("paper_sizes.txt")}
+    n = int(d["inputs"])
+    out = o.remap(np.zeros((1, n * (n + 1) // 2, 2), np.int64), np.arange(n, dtype=np.int32))
+    assert out[0].size // 2 == int(d["visibilities_per_channel"])
+
+
 ALL_PINS = [pin_decode_table, pin_library_matmul, pin_hermitian, pin_autos,
             pin_constant_closed_form, pin_rank_one, pin_additivity, pin_permutation,
-            pin_tone_phase, pin_invalid_reading, pin_paper_sizes, pin_brute_force]
+            pin_tone_phase, pin_invalid_reading, pin_paper_sizes, pin_brute_force,
+            pin_beam_autos, pin_beam_brute_force, pin_pfb_order_printed,
+            pin_remap_natural_order, pin_remap_paper_count]

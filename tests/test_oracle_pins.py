@@ -70,6 +70,21 @@ MUTANTS = {
     "invalid_flag_ignored": (
         r"if \(zero_invalid && \(hi == 8u \|\| lo == 8u\)\)",
         "if (0)"),
+    "beam_drops_imaginary_power": (
+        r"p \+= \(int64_t\)r \* r \+ \(int64_t\)m \* m;",
+        "p += (int64_t)r * r;"),
+    "beam_window_off_by_one": (
+        r"for \(int t = k \* n_avg; t < \(k \+ 1\) \* n_avg; \+\+t\)",
+        "for (int t = k * n_avg; t <= (k + 1) * n_avg && t < T; ++t)"),
+    "remap_conjugate_not_applied": (
+        r"im -= vf\[2 \* k \+ 1\];",
+        "im += vf[2 * k + 1];"),
+    "remap_uses_permutation_not_inverse": (
+        r"const int i = pos\[2 \* s1 \+ p1\], j = pos\[2 \* s2 \+ p2\];",
+        "const int i = nat_of_pfb[2 * s1 + p1], j = nat_of_pfb[2 * s2 + p2];"),
+    "remap_pols_swapped": (
+        r"\(\(int64_t\)g \* Q \+ \(int64_t\)s1 \* \(s1 \+ 1\) / 2 \+ s2\) \* 4 \+ p1 \* 2 \+ p2\)",
+        "((int64_t)g * Q + (int64_t)s1 * (s1 + 1) / 2 + s2) * 4 + p2 * 2 + p1)"),
     "accumulate_overwrites": (
         r"vf\[2 \* p\] \+= sre;\n                vf\[2 \* p \+ 1\] \+= sim;",
         "vf[2 * p] = sre;\n                vf[2 * p + 1] = sim;"),
