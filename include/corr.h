@@ -312,6 +312,51 @@ int corr_batch_graph_capture(corr_batch *b, const uint8_t *const *d_volt, const 
 int corr_graph_launch(void *graph_exec, void *stream);
 int corr_graph_destroy(void *graph_exec);
 
+/* --------------------------------------------------- other modes and output -- */
+
+/*
+ * Incoherent beam (Section 3.4: one of the XMAC's modes besides correlation):
+ * the total power of all inputs per channel and sample, summed over n_avg
+ * consecutive samples:
+ *
+ *   d_beam[k][f] = sum over t in [k n_avg, (k+1) n_avg), over n < n_inputs, of |x_n(t,f)|^2
+ *
+ * d_volt: device uint8 [n_time][n_chan][n_inputs] (Appendix A encoding, real
+ * part in the high nibble); d_beam: device int32 [n_time / n_avg][n_chan].
+ * flags: CORR_ZERO_INVALID (samples with a nibble code 8 contribute 0) or 0.
+ * CORR_E_ARG if n_time is not a multiple of n_avg or 128 n_avg n_inputs
+ * reaches 2^31 (the int32 bound).  Asynchronous, allocates nothing.
+ */
+int corr_incoherent_beam(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs, int n_avg,
+                         unsigned flags, int32_t *d_beam, void *stream);
+
+#define CORR_REMAP_MAX_DUMPS 8
+/*
+ * Output remap (Appendix C, "GPU Output"): the X-engine correlates the inputs
+ * in PFB order, so its triangle is over PFB positions; this writes the
+ * products per station pair in natural input order, conjugating those the
+ * triangle holds only as conjugates, and optionally integrates further over
+ * f_avg adjacent channels and over n_dumps consecutive dumps (Section 3.4.3:
+ * "integrate by a factor of two in each dimension" is f_avg = n_dumps = 2):
+ *
+ *   d_out[g][s1(s1+1)/2 + s2][p1][p2][re,im] = sum over d < n_dumps and the
+ *       f_avg channels f of group g of  V_{2 s1 + p1, 2 s2 + p2}(f),   s2 <= s1
+ *
+ * d_tri: host array of n_dumps (<= CORR_REMAP_MAX_DUMPS) device pointers to
+ * int32 [n_chan][n_inputs(n_inputs+1)/2][2] triangles as corr_dump writes
+ * them.  d_nat_of_pfb: device int32 [n_inputs], the natural input carried at
+ * each PFB position, or NULL for the Appendix A order (position k of each
+ * PFB's 64 carries input (k mod 4) * 16 + k div 4; PFB blocks concatenated,
+ * Appendix B), which needs n_inputs % 64 == 0.  Reading: natural input a is
+ * station a / 2, polarisation a % 2.  d_out: device int32
+ * [n_chan / f_avg][S(S+1)/2][2][2][2], S = n_inputs / 2 (33024 complex
+ * products per channel at 256 inputs).  Sums are int32: the caller keeps
+ * n_dumps f_avg 128 n_time below 2^31.  A table that is not a permutation
+ * gives undefined products but no out-of-bounds access.  Asynchronous.
+ */
+int corr_remap(const int32_t *const *d_tri, int n_dumps, int n_inputs, int n_chan, int f_avg,
+               const int32_t *d_nat_of_pfb, int32_t *d_out, void *stream);
+
 /* ------------------------------------------------------- no device allocation -- */
 
 /* Size of the library's static device scratch used by corr_xmac_noalloc. */

@@ -110,6 +110,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_set_state": ([vp, vp, c_size, vp], c_int),
             "corr_unpack": ([vp, c_int, c_int, c_int, vp, ctypes.c_uint, vp], c_int),
             "corr_xmac_noalloc": ([vp, c_int, c_int, c_int, vp, ctypes.c_uint, vp], c_int),
+            "corr_incoherent_beam": ([vp, c_int, c_int, c_int, c_int, ctypes.c_uint, vp, vp], c_int),
+            "corr_remap": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, vp, vp, vp], c_int),
             "corr_batch_create": ([c_int, ctypes.POINTER(ArrayDesc)], vp),
             "corr_batch_destroy": ([vp], c_int),
             "corr_batch_workspace_bytes": ([vp], c_size),
@@ -498,6 +500,60 @@ class Batch:
             self.close()
         except Exception:
             pass
+
+
+def incoherent_beam(volt: torch.Tensor, n_avg: int = 1, zero_invalid: bool = False,
+                    out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Total power of all inputs per channel: int32 [T / n_avg][F] (corr_incoherent_beam)."""
+    if volt.dtype != torch.uint8 or volt.dim() != 3 or not volt.is_contiguous() or not volt.is_cuda:
+        raise ValueError("volt must be a contiguous uint8 CUDA tensor [T][F][N]")
+    T, F, N = volt.shape
+    if n_avg < 1 or T % n_avg:
+        raise ValueError("n_time must be a multiple of n_avg")
+    shape = (T // n_avg, F)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.int32, device=volt.device)
+    elif out.dtype != torch.int32 or tuple(out.shape) != shape or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous int32 {shape} tensor")
+    _check(load().corr_incoherent_beam(ctypes.c_void_p(volt.data_ptr()), T, F, N, n_avg,
+                                       ZERO_INVALID if zero_invalid else 0,
+                                       ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
+           "corr_incoherent_beam")
+    return out
+
+
+def remap(tris, nat_of_pfb: torch.Tensor | None = None, f_avg: int = 1,
+          out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """Station-pair products in natural input order, summed over the dumps in
+    `tris` (one [F][P][2] int32 tensor or a list of them) and f_avg channels:
+    int32 [F / f_avg][S(S+1)/2][2][2][2] (corr_remap).  nat_of_pfb: int32
+    tensor [N] on the device, or None for the Appendix A PFB order."""
+    if isinstance(tris, torch.Tensor):
+        tris = [tris]
+    if not tris or len(tris) > 8:
+        raise ValueError("between 1 and 8 triangles")
+    F, P, two = tris[0].shape
+    N = int(round(((8 * P + 1) ** 0.5 - 1) / 2))
+    for t in tris:
+        if (t.dtype != torch.int32 or tuple(t.shape) != (F, P, 2) or not t.is_contiguous()
+                or not t.is_cuda or N * (N + 1) // 2 != P):
+            raise ValueError("triangles must be contiguous int32 CUDA tensors [F][N(N+1)/2][2]")
+    S = N // 2
+    shape = (F // max(f_avg, 1), S * (S + 1) // 2, 2, 2, 2)
+    if out is None:
+        out = torch.empty(shape, dtype=torch.int32, device=tris[0].device)
+    elif out.dtype != torch.int32 or tuple(out.shape) != shape or not out.is_contiguous():
+        raise ValueError(f"out must be a contiguous int32 {shape} tensor")
+    perm_ptr = ctypes.c_void_p(0)
+    if nat_of_pfb is not None:
+        if (nat_of_pfb.dtype != torch.int32 or tuple(nat_of_pfb.shape) != (N,) or not nat_of_pfb.is_cuda
+                or not nat_of_pfb.is_contiguous()):
+            raise ValueError(f"nat_of_pfb must be a contiguous int32 CUDA tensor [{N}]")
+        perm_ptr = ctypes.c_void_p(nat_of_pfb.data_ptr())
+    ptrs = (ctypes.c_void_p * len(tris))(*[t.data_ptr() for t in tris])
+    _check(load().corr_remap(ptrs, len(tris), N, F, f_avg, perm_ptr, ctypes.c_void_p(out.data_ptr()),
+                             _stream_handle(stream)), "corr_remap")
+    return out
 
 
 def unpack(volt: torch.Tensor, zero_invalid: bool = False, stream=None) -> torch.Tensor:

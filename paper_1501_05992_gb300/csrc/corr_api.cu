@@ -665,6 +665,34 @@ int corr_set_state(corr_ctx *c, const void *h_buf, size_t bytes, void *stream)
     return ret(CORR_OK);
 }
 
+int corr_incoherent_beam(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs, int n_avg,
+                         unsigned flags, int32_t *d_beam, void *stream)
+{
+    if (n_time < 0 || n_chan < 1 || n_chan > (1 << 24) || n_inputs < 1 || n_inputs > 65536 || n_avg < 1 ||
+        n_time % n_avg != 0 || (long long)n_avg * n_inputs * 128LL >= (1LL << 31) ||
+        (flags & ~CORR_ZERO_INVALID))
+        return ret(CORR_E_ARG);
+    if (n_time == 0) return ret(CORR_OK);
+    if (!d_volt || !d_beam) return ret(CORR_E_ARG);
+    const cudaError_t e = launch_beam(d_volt, n_time, n_chan, n_inputs, n_avg, (flags & CORR_ZERO_INVALID) != 0,
+                                      d_beam, static_cast<cudaStream_t>(stream));
+    return ret(e == cudaSuccess ? CORR_OK : cuda_fail(e));
+}
+
+int corr_remap(const int32_t *const *d_tri, int n_dumps, int n_inputs, int n_chan, int f_avg,
+               const int32_t *d_nat_of_pfb, int32_t *d_out, void *stream)
+{
+    if (!d_tri || !d_out || n_dumps < 1 || n_dumps > CORR_REMAP_MAX_DUMPS || n_inputs < 2 ||
+        n_inputs % 2 != 0 || n_inputs > 8192 || n_chan < 1 || n_chan > 65535 || f_avg < 1 ||
+        n_chan % f_avg != 0 || (!d_nat_of_pfb && n_inputs % 64 != 0))
+        return ret(CORR_E_ARG);
+    for (int d = 0; d < n_dumps; ++d)
+        if (!d_tri[d]) return ret(CORR_E_ARG);
+    const cudaError_t e = launch_remap(d_tri, n_dumps, n_inputs, n_chan, f_avg, d_nat_of_pfb, d_out,
+                                       static_cast<cudaStream_t>(stream));
+    return ret(e == cudaSuccess ? CORR_OK : cuda_fail(e));
+}
+
 int corr_unpack(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs, int8_t *d_out,
                 unsigned flags, void *stream)
 {

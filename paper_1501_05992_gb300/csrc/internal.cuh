@@ -96,6 +96,18 @@ cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool 
                            int32_t *acc, bool fresh, DeviceStatus *status, const TcOptions &opt,
                            cudaStream_t s);
 
+// Incoherent beam: out[k][f] = sum of |x|^2 over inputs and the n_avg samples
+// of block k (n_time / n_avg blocks), int32.
+cudaError_t launch_beam(const uint8_t *volt, int n_time, int n_chan, int n, int n_avg, bool zero_invalid,
+                        int32_t *out, cudaStream_t s);
+
+// Output remap of n_dumps PFB-order triangles tri[d] (int32 [n_chan][P][2])
+// into station-pair order summed over dumps and f_avg channels:
+// out int32 [n_chan / f_avg][S(S+1)/2][2][2][2], S = n / 2.  nat_of_pfb
+// (device, n entries) or NULL for the Appendix A order.  n_dumps <= 8.
+cudaError_t launch_remap(const int32_t *const *tri, int n_dumps, int n, int n_chan, int f_avg,
+                         const int32_t *nat_of_pfb, int32_t *out, cudaStream_t s);
+
 // Record `status` as the calling thread's last error and return it.
 int set_last_error(int status);
 

@@ -1,0 +1,87 @@
+"""The incoherent beam and the output remap (with channel and dump
+averaging) against the oracle, element by element."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+from paper_1501_05992_gb300 import corr
+from synth import voltgen as vg
+from synth.gpu import DeviceGenerator
+
+pytestmark = pytest.mark.gpu
+
+
+def _rand(shape, seed):
+    return np.random.default_rng(seed).integers(0, 256, shape, dtype=np.uint8)
+
+
+@pytest.mark.parametrize("shape,n_avg", [((36, 5, 48), 1), ((36, 5, 48), 4), ((20, 3, 13), 5),
+                                         ((7, 300, 256), 7), ((1, 1, 1), 1)])
+@pytest.mark.parametrize("zero_invalid", [False, True])
+def test_beam_exact(shape, n_avg, zero_invalid):
+    volt = _rand(shape, sum(shape) + n_avg)
+    volt.reshape(-1)[::11] = 0x88
+    volt.reshape(-1)[5::13] = 0x38
+    got = corr.incoherent_beam(torch.from_numpy(volt).cuda(), n_avg, zero_invalid).cpu().numpy()
+    want = oracle.beam(volt, n_avg, zero_invalid)
+    assert np.array_equal(got, want)
+
+
+def test_beam_full_band_sampled_channels():
+    N, F, T = 256, 3072, 5000
+    volt = DeviceGenerator(vg.gauss3_params(1503, N, F)).make(0, T)
+    got = corr.incoherent_beam(volt, 1).cpu().numpy()
+    torch.cuda.synchronize()
+    chans = [0, 1, 1535, 3071]
+    sub = volt[:, chans].cpu().numpy()
+    want = oracle.beam(sub, 1)
+    assert np.array_equal(got[:, chans], want)
+
+
+def test_beam_arguments():
+    v = torch.zeros((10, 2, 16), dtype=torch.uint8, device="cuda")
+    with pytest.raises(ValueError):
+        corr.incoherent_beam(v, 3)
+
+
+def _tri_of(volt_np, path="auto"):
+    T, F, N = volt_np.shape
+    c = corr.Correlator(N, F, max(T, 1), path=path)
+    out = c.integrate(torch.from_numpy(volt_np).cuda())
+    c.sync()
+    c.close()
+    return out
+
+
+@pytest.mark.parametrize("N,F,T", [(8, 4, 30), (128, 6, 200), (70, 2, 33)])
+@pytest.mark.parametrize("f_avg,n_dumps", [(1, 1), (2, 2), (1, 3)])
+def test_remap_exact_custom_order(N, F, T, f_avg, n_dumps):
+    if F % f_avg:
+        pytest.skip("channels not divisible")
+    rng = np.random.default_rng(N + F + T + f_avg + n_dumps)
+    perm = rng.permutation(N).astype(np.int32)
+    volts = [_rand((T, F, N), 7 * d + N) for d in range(n_dumps)]
+    tris = [_tri_of(v) for v in volts]
+    got = corr.remap(tris, torch.from_numpy(perm).cuda(), f_avg=f_avg).cpu().numpy()
+    want = oracle.remap(np.stack([oracle.xmac(v) for v in volts]), perm, f_avg=f_avg)
+    assert np.array_equal(got, oracle.to_int32(want))
+
+
+def test_remap_default_pfb_order_full_channel():
+    N, F, T = 256, 4, 300
+    volt = _rand((T, F, N), 77)
+    tri = _tri_of(volt)
+    got = corr.remap(tri).cpu().numpy()
+    want = oracle.remap(oracle.xmac(volt), oracle.pfb_order(N))
+    assert got.shape == (F, 128 * 129 // 2, 2, 2, 2)
+    assert got[0].size // 2 == 33024                      # products per channel (Section 3.4.3)
+    assert np.array_equal(got, oracle.to_int32(want))
+
+
+def test_remap_arguments():
+    t = torch.zeros((2, 70 * 71 // 2, 2), dtype=torch.int32, device="cuda")
+    with pytest.raises(corr.CorrError):
+        corr.remap(t)                                         # default order needs whole PFBs
+    with pytest.raises(corr.CorrError):
+        corr.remap(t, torch.arange(70, dtype=torch.int32, device="cuda"), f_avg=3)
