@@ -59,6 +59,8 @@ def parse_args():
     ap.add_argument("--cpu-seconds", type=float, default=12.0,
                     help="target CPU time of the oracle baseline sample")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the incoherent-beam and output-remap measurements")
     return ap.parse_args()
 
 
@@ -287,6 +289,51 @@ def roofline_for(path, ops_per_launch, avg_ms, peaks, src, sm_count):
                          f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"}
 
 
+def _time_ms(fn, stream, reps=5):
+    """Median CUDA-event time of fn() on `stream` after one warm-up call."""
+    with torch.cuda.stream(stream):
+        fn()
+    stream.synchronize()
+    ts = []
+    for _ in range(reps):
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        with torch.cuda.stream(stream):
+            fn()
+        e1.record(stream)
+        stream.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return statistics.median(ts)
+
+
+def measure_extras(arrays, volts, outs, stream, dev, peaks, src):
+    """The other modes on the first array's first integration, against the HBM
+    roofline: the incoherent beam (reads every voltage byte once, writes one
+    int32 per channel and sample) and the output remap with 2 x 2 averaging
+    (reads two dumps' triangles, writes the station-order products of channel
+    pairs).  Not part of the timed step."""
+    n, f, t = arrays[0]
+    hbm = peaks.get("hbm_gbs")
+    res = {}
+    volt = volts[0][:t]
+    beam = torch.empty((t, f), dtype=torch.int32, device=dev)
+    ms = _time_ms(lambda: corr.incoherent_beam(volt, 1, out=beam, stream=stream), stream)
+    nbytes = n * f * t + 4 * f * t
+    res["incoherent_beam"] = {"ms": ms, "bytes": nbytes, "gbs": nbytes / ms / 1e6,
+                              "frac": (nbytes / ms / 1e6) / hbm if hbm else None,
+                              "peak_gbs": hbm, "bound": "hbm"}
+    if n % 64 == 0 and f % 2 == 0:
+        tris = [outs[0][0], outs[1][0]]
+        S = n // 2
+        rm = torch.empty((f // 2, S * (S + 1) // 2, 2, 2, 2), dtype=torch.int32, device=dev)
+        ms = _time_ms(lambda: corr.remap(tris, None, 2, out=rm, stream=stream), stream)
+        nbytes = 2 * f * n * (n + 1) // 2 * 8 + rm.numel() * 4
+        res["remap_2x2"] = {"ms": ms, "bytes": nbytes, "gbs": nbytes / ms / 1e6,
+                            "frac": (nbytes / ms / 1e6) / hbm if hbm else None,
+                            "peak_gbs": hbm, "bound": "hbm"}
+    return res
+
+
 def run_ours(args, world, rank, local):
     import torch
     from paper_1501_05992_gb300 import autotune, corr
@@ -457,6 +504,10 @@ def run_ours(args, world, rank, local):
                        "integration per array, re-sent for each integration of the step"}
         del h_volts, h_outs
 
+    extras = None
+    if not args.no_extras and rank == 0:
+        extras = measure_extras(arrays, volts, outs, stream, dev, peaks, src)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         n, f, t = arrays[0]
@@ -476,6 +527,8 @@ def run_ours(args, world, rank, local):
             "gpu_launches": launches_per_step * args.steps, "clocks": clk, "roofline": roof,
             "cpu_baseline": cpu, "e2e": e2e, "kernel_ms": kernel_ms,
         }
+        if extras:
+            line["extras"] = extras
         if tuned:
             line["autotune"] = tuned
         print(json.dumps(line), flush=True)

@@ -82,6 +82,8 @@ class OracleLib:
         lib.oracle_beam.restype = c_int
         lib.oracle_remap.argtypes = [i64p, c_int, c_int, c_int, c_int, i32p, i64p]
         lib.oracle_remap.restype = c_int
+        lib.oracle_ingest.argtypes = [u8p, ctypes.c_int64, c_int, u8p, i64p]
+        lib.oracle_ingest.restype = c_int
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = c_int
         self.lib = lib
@@ -163,6 +165,17 @@ class OracleLib:
             raise ValueError("oracle_remap: bad arguments")
         return out
 
+    def ingest(self, packets: np.ndarray, bank: int):
+        """One bank of 264-byte PFB packets (uint8 [n][264]) -> the voltage block
+        uint8 [500][3072][256] and the counters (good, bad header, bad checksum,
+        bad field, duplicate, missing slots)."""
+        pk = np.ascontiguousarray(packets, dtype=np.uint8).reshape(-1, 264)
+        volt = np.zeros((500, 3072, 256), np.uint8)
+        counters = np.zeros(6, np.int64)
+        if self.lib.oracle_ingest(_u8(pk), pk.shape[0], int(bank), _u8(volt), _i64(counters)) != 0:
+            raise ValueError("oracle_ingest: bad arguments")
+        return volt, counters
+
     def threads(self) -> int:
         """OpenMP threads the triangle routine uses."""
         return int(self.lib.oracle_threads())
@@ -198,6 +211,10 @@ def beam(volt, n_avg=1, zero_invalid=False):
 
 def remap(tri, nat_of_pfb, f_avg=1):
     return default().remap(tri, nat_of_pfb, f_avg)
+
+
+def ingest(packets, bank):
+    return default().ingest(packets, bank)
 
 
 def pfb_order(n_inputs: int) -> np.ndarray:

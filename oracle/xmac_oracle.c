@@ -286,6 +286,101 @@ int oracle_remap(const int64_t *tri, int N, int F, int n_dumps, int f_avg, const
     return 0;
 }
 
+/*
+ * Packet ingest (Appendix A "Data Format"; Appendix B): turn one 50 ms bank of
+ * PFB packets into the assembled voltage block volt[500][3072][256] (frame,
+ * fine channel, input in PFB order).  A packet is 264 bytes: the header word
+ * 0x0800, word two and word three with the second tick and the counters, 256
+ * sample bytes (four fine channels of 64 PFB inputs), and a 16-bit checksum,
+ * the XOR of the 128 data words.  Readings where the appendix is silent:
+ * words are most significant byte first; word two holds sec_tick (bit 0),
+ * pfb_id (bits 4-5), mgt_id (bits 6-8) and mgt_bank (bits 9-13); word three
+ * holds mgt_frame (bits 0-8: values 0-499 need 9 bits), mgt_group (bits
+ * 9-10) and mgt_channel (bits 11-15); data byte 64 f2 + k is fine channel
+ * 128 mgt_channel + 16 mgt_id + 4 mgt_group + f2, input 64 pfb_id + k.
+ *
+ * A packet is rejected (counted, not written) if its header is not 0x0800,
+ * its checksum does not match, or a field is out of range for this bank
+ * (mgt_bank != bank, mgt_channel >= 24, mgt_frame >= 500, or sec_tick set on
+ * a packet that is not the second's first).  Every (frame, group of four
+ * channels, PFB) slot that no good packet filled is written with the byte
+ * 0x88 (both parts code 8, the appendix's invalid marker).  counters:
+ * [0] good, [1] bad header, [2] bad checksum, [3] bad field, [4] duplicate
+ * (a slot filled again; the later packet's bytes stay), [5] missing slots.
+ */
+#define PKT_FRAMES 500
+#define PKT_CHANNELS 3072
+#define PKT_INPUTS 256
+#define PKT_GROUPS (PKT_CHANNELS / 4)
+
+int oracle_ingest(const uint8_t *pk, int64_t n_packets, int bank, uint8_t *volt, int64_t *counters)
+{
+    if ((!pk && n_packets > 0) || n_packets < 0 || !volt || !counters || bank < 0 || bank > 31)
+        return -1;
+    const int64_t n_slots = (int64_t)PKT_FRAMES * PKT_GROUPS * 4;
+    uint8_t *seen = (uint8_t *)calloc((size_t)n_slots, 1);
+    if (!seen)
+        return -1;
+    for (int c = 0; c < 6; ++c)
+        counters[c] = 0;
+    for (int64_t q = 0; q < n_packets; ++q) {
+        const uint8_t *b = pk + q * 264;
+        const unsigned header = ((unsigned)b[0] << 8) | b[1];
+        if (header != 0x0800u) {
+            counters[1]++;
+            continue;
+        }
+        unsigned xhi = 0, xlo = 0;
+        for (int w = 0; w < 128; ++w) {
+            xhi ^= b[6 + 2 * w];
+            xlo ^= b[7 + 2 * w];
+        }
+        if (xhi != b[262] || xlo != b[263]) {
+            counters[2]++;
+            continue;
+        }
+        const unsigned w2 = ((unsigned)b[2] << 8) | b[3];
+        const unsigned w3 = ((unsigned)b[4] << 8) | b[5];
+        const int tick = (int)(w2 & 1u);
+        const int pfb = (int)((w2 >> 4) & 3u);
+        const int mgt = (int)((w2 >> 6) & 7u);
+        const int bnk = (int)((w2 >> 9) & 31u);
+        const int frame = (int)(w3 & 511u);
+        const int grp = (int)((w3 >> 9) & 3u);
+        const int chan = (int)((w3 >> 11) & 31u);
+        const int first = bnk == 0 && chan == 0 && grp == 0 && frame == 0;
+        if (bnk != bank || chan >= 24 || frame >= PKT_FRAMES || (tick && !first)) {
+            counters[3]++;
+            continue;
+        }
+        const int cgroup = 32 * chan + 4 * mgt + grp;          /* fine channel / 4 */
+        const int64_t slot = ((int64_t)frame * PKT_GROUPS + cgroup) * 4 + pfb;
+        if (seen[slot])
+            counters[4]++;
+        seen[slot] = 1;
+        counters[0]++;
+        for (int f2 = 0; f2 < 4; ++f2) {
+            const int f = 4 * cgroup + f2;
+            for (int k = 0; k < 64; ++k)
+                volt[((int64_t)frame * PKT_CHANNELS + f) * PKT_INPUTS + 64 * pfb + k] = b[6 + 64 * f2 + k];
+        }
+    }
+    for (int frame = 0; frame < PKT_FRAMES; ++frame) {
+        for (int cgroup = 0; cgroup < PKT_GROUPS; ++cgroup) {
+            for (int pfb = 0; pfb < 4; ++pfb) {
+                if (seen[((int64_t)frame * PKT_GROUPS + cgroup) * 4 + pfb])
+                    continue;
+                counters[5]++;
+                for (int f2 = 0; f2 < 4; ++f2)
+                    for (int k = 0; k < 64; ++k)
+                        volt[((int64_t)frame * PKT_CHANNELS + 4 * cgroup + f2) * PKT_INPUTS + 64 * pfb + k] = 0x88;
+            }
+        }
+    }
+    free(seen);
+    return 0;
+}
+
 /* Number of OpenMP threads the triangle routine would use (1 without OpenMP). */
 int oracle_threads(void)
 {

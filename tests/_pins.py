@@ -326,8 +326,81 @@ def pin_remap_paper_count(o):
     assert out[0].size // 2 == int(d["visibilities_per_channel"])
 
 
+def _golden_packet():
+    pk = np.zeros(264, np.uint8)
+    bank, samples = None, []
+    for row in read_table("pfb_packet_example.txt"):
+        if row[0] == "bank":
+            bank = int(row[1])
+        elif row[0] == "bytes":
+            pk[int(row[1])] = int(row[2], 16)
+        elif row[0] == "sample":
+            samples.append((int(row[1]), int(row[2]), int(row[3]), int(row[4], 16)))
+    return pk, bank, samples
+
+
+def pin_ingest_golden_packet(o):
+    """A packet written out by hand from Appendix A lands where the appendix
+    says; every slot no packet filled is marked invalid (0x88)."""
+    pk, bank, samples = _golden_packet()
+    volt, cnt = o.ingest(pk[None], bank)
+    for t, f, n, v in samples:
+        assert volt[t, f, n] == v
+    assert cnt[0] == 1 and cnt[1:5].sum() == 0 and cnt[5] == 500 * 768 * 4 - 1
+    slot = volt[421, 2524:2528, 128:192]
+    assert np.count_nonzero(slot) == 4
+    assert volt[421, 2524, 127] == 0x88 and volt[421, 2528, 128] == 0x88 and volt[0, 0, 0] == 0x88
+    # the same packet for another bank is rejected as out of range
+    _, cnt = o.ingest(pk[None], bank + 1)
+    assert cnt[3] == 1 and cnt[0] == 0
+
+
+def pin_ingest_rejections(o):
+    pk, bank, _ = _golden_packet()
+    bad = np.stack([pk.copy() for _ in range(5)])
+    bad[0, 0] = 0x09                      # header
+    bad[1, 100] ^= 0x01                   # data byte: checksum mismatch
+    bad[2, 263] ^= 0x10                   # checksum byte
+    bad[3, 3] |= 0x01                     # sec_tick on a packet that is not the second's first
+    w3 = (int(bad[4, 4]) << 8 | int(bad[4, 5])) & ~0x1FF | 500          # frame 500
+    bad[4, 4], bad[4, 5] = w3 >> 8, w3 & 0xFF
+    _, cnt = o.ingest(bad, bank)
+    assert cnt.tolist() == [0, 1, 2, 2, 0, 500 * 768 * 4]
+    volt, cnt = o.ingest(np.stack([pk, pk]), bank)          # a repeated packet
+    assert cnt[0] == 2 and cnt[4] == 1 and volt[421, 2524, 128] == 0x12
+
+
+def pin_ingest_round_trip(o):
+    """Packets built from a block by the numpy packetiser (a separate
+    implementation of the same format) ingest back to that block."""
+    from synth import packets as pkts
+    d = {r[0]: r[1:] for r in read_table("paper_packets.txt")}
+    block = _rng(37).integers(0, 256, (500, 3072, 256), dtype=np.uint8)
+    lanes = [(0, 0), (1, 3), (3, 7)]
+    stream = np.concatenate([pkts.lane_packets(block, p, m, 5) for p, m in lanes])
+    per_lane = int(d["packets_per_lane_per_bank"][0])
+    assert stream.shape == (len(lanes) * per_lane, int(d["packet_bytes"][0]))
+    assert int(d["packets_per_lane_per_second"][0]) == 20 * per_lane
+    volt, cnt = o.ingest(stream[::-1], 5)                   # arrival order does not matter
+    assert cnt.tolist() == [stream.shape[0], 0, 0, 0, 0, 500 * 768 * 4 - stream.shape[0]]
+    for p, m in lanes:
+        chans = (128 * np.arange(24)[:, None] + 16 * m + np.arange(16)[None, :]).reshape(-1)
+        assert np.array_equal(volt[:, chans, 64 * p:64 * p + 64], block[:, chans, 64 * p:64 * p + 64])
+    untouched = volt[:, :, 128:192].copy()                  # pfb 2 sent nothing
+    assert (untouched == 0x88).all()
+    # the channel groups a lane carries are the printed ones: lane (pfb 0, mgt 0)
+    lane = pkts.lane_packets(block, 0, 0, 5)
+    v0, c0 = o.ingest(lane, 5)
+    filled = np.flatnonzero((v0[:, :, :64] != 0x88).any(axis=(0, 2)))
+    starts = filled[::4]
+    assert starts[:8].tolist() == [int(x) for x in d["lane0_group_starts"]]
+    assert starts[-4:].tolist() == [int(x) for x in d["lane0_group_ends"]]
+    assert len(starts) == int(d["channel_groups_per_lane"][0])
+
+
 ALL_PINS = [pin_decode_table, pin_library_matmul, pin_hermitian, pin_autos,
             pin_constant_closed_form, pin_rank_one, pin_additivity, pin_permutation,
             pin_tone_phase, pin_invalid_reading, pin_paper_sizes, pin_brute_force,
             pin_beam_autos, pin_beam_brute_force, pin_pfb_order_printed,
-            pin_remap_natural_order, pin_remap_paper_count]
+            pin_remap_natural_order, pin_remap_paper_count, pin_ingest_golden_packet,
+            pin_ingest_rejections, pin_ingest_round_trip]

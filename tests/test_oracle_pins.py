@@ -85,6 +85,21 @@ MUTANTS = {
     "remap_pols_swapped": (
         r"\(\(int64_t\)g \* Q \+ \(int64_t\)s1 \* \(s1 \+ 1\) / 2 \+ s2\) \* 4 \+ p1 \* 2 \+ p2\)",
         "((int64_t)g * Q + (int64_t)s1 * (s1 + 1) / 2 + s2) * 4 + p2 * 2 + p1)"),
+    "ingest_channel_and_input_swapped": (
+        r"= b\[6 \+ 64 \* f2 \+ k\];",
+        "= b[6 + 4 * k + f2 % 4 + 0 * f2];"),
+    "ingest_group_stride": (
+        r"const int cgroup = 32 \* chan \+ 4 \* mgt \+ grp;",
+        "const int cgroup = 32 * chan + 4 * mgt + 2 * grp;"),
+    "ingest_checksum_bytes_swapped": (
+        r"if \(xhi != b\[262\] \|\| xlo != b\[263\]\)",
+        "if (xhi != b[263] || xlo != b[262])"),
+    "ingest_missing_not_marked": (
+        r"volt\[\(\(int64_t\)frame \* PKT_CHANNELS \+ 4 \* cgroup \+ f2\) \* PKT_INPUTS \+ 64 \* pfb \+ k\] = 0x88;",
+        "(void)0;"),
+    "ingest_frame_five_bits": (
+        r"const int frame = \(int\)\(w3 & 511u\);",
+        "const int frame = (int)(w3 & 31u);"),
     "accumulate_overwrites": (
         r"vf\[2 \* p\] \+= sre;\n                vf\[2 \* p \+ 1\] \+= sim;",
         "vf[2 * p] = sre;\n                vf[2 * p + 1] = sim;"),
