@@ -291,6 +291,7 @@ def roofline_for(path, ops_per_launch, avg_ms, peaks, src, sm_count):
 
 def _time_ms(fn, stream, reps=5):
     """Median CUDA-event time of fn() on `stream` after one warm-up call."""
+    import torch
     with torch.cuda.stream(stream):
         fn()
     stream.synchronize()
@@ -306,27 +307,47 @@ def _time_ms(fn, stream, reps=5):
     return statistics.median(ts)
 
 
-def measure_extras(arrays, volts, outs, stream, dev, peaks, src):
-    """The other modes on the first array's first integration, against the HBM
-    roofline: the incoherent beam (reads every voltage byte once, writes one
-    int32 per channel and sample) and the output remap with 2 x 2 averaging
-    (reads two dumps' triangles, writes the station-order products of channel
-    pairs).  Not part of the timed step."""
+def measure_extras(arrays, volts, outs, stream_, dev, peaks, src):
+    """The stages around the X-engine on the first array's first integration,
+    against the HBM roofline: the incoherent beam (reads every voltage byte
+    once, writes one int32 per channel and sample), the packet ingest of one
+    50 ms bank (reads the packets, writes the voltage block) and the output
+    remap with 2 x 2 averaging (reads two dumps' triangles, writes the
+    station-order products of channel pairs).  Not part of the timed step."""
+    import torch
+    from paper_1501_05992_gb300 import corr
     n, f, t = arrays[0]
     hbm = peaks.get("hbm_gbs")
     res = {}
     volt = volts[0][:t]
     beam = torch.empty((t, f), dtype=torch.int32, device=dev)
-    ms = _time_ms(lambda: corr.incoherent_beam(volt, 1, out=beam, stream=stream), stream)
+    ms = _time_ms(lambda: corr.incoherent_beam(volt, 1, out=beam, stream=stream_), stream_)
     nbytes = n * f * t + 4 * f * t
     res["incoherent_beam"] = {"ms": ms, "bytes": nbytes, "gbs": nbytes / ms / 1e6,
                               "frac": (nbytes / ms / 1e6) / hbm if hbm else None,
                               "peak_gbs": hbm, "bound": "hbm"}
+    if (n, f) == (256, 3072) and t >= 500:
+        # packet ingest of one 50 ms bank: the bank's packets built on the host
+        # by the synthetic packetiser from the first 500 samples
+        from synth import packets as pkts
+        stream = torch.from_numpy(pkts.packetise(volts[0][:500].cpu().numpy(), 0)).to(dev)
+        blk = torch.empty((500, f, n), dtype=torch.uint8, device=dev)
+        seen = torch.empty(corr.PKT_SLOTS, dtype=torch.int32, device=dev)
+        cnt = torch.empty(6, dtype=torch.int32, device=dev)
+        torch.cuda.synchronize(dev)
+        ms = _time_ms(lambda: corr.ingest_packets(stream, 0, blk, seen, cnt, stream=stream_), stream_)
+        ok = bool(torch.equal(blk, volts[0][:500])) and cnt.tolist()[0] == stream.shape[0]
+        nbytes = stream.numel() + blk.numel()
+        res["packet_ingest"] = {"ms": ms, "bytes": nbytes, "gbs": nbytes / ms / 1e6,
+                                "frac": (nbytes / ms / 1e6) / hbm if hbm else None,
+                                "peak_gbs": hbm, "bound": "hbm", "packets": int(stream.shape[0]),
+                                "round_trip_exact": ok}
+        del stream, blk, seen
     if n % 64 == 0 and f % 2 == 0:
         tris = [outs[0][0], outs[1][0]]
         S = n // 2
         rm = torch.empty((f // 2, S * (S + 1) // 2, 2, 2, 2), dtype=torch.int32, device=dev)
-        ms = _time_ms(lambda: corr.remap(tris, None, 2, out=rm, stream=stream), stream)
+        ms = _time_ms(lambda: corr.remap(tris, None, 2, out=rm, stream=stream_), stream_)
         nbytes = 2 * f * n * (n + 1) // 2 * 8 + rm.numel() * 4
         res["remap_2x2"] = {"ms": ms, "bytes": nbytes, "gbs": nbytes / ms / 1e6,
                             "frac": (nbytes / ms / 1e6) / hbm if hbm else None,

@@ -330,6 +330,48 @@ int corr_graph_destroy(void *graph_exec);
 int corr_incoherent_beam(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs, int n_avg,
                          unsigned flags, int32_t *d_beam, void *stream);
 
+/*
+ * Packet ingest (Appendix A "Data Format", Appendix B): one 50 ms bank of PFB
+ * packets into the voltage block the X-engine reads.
+ *
+ * Packet (CORR_PKT_BYTES = 264): header word 0x0800; word two: sec_tick
+ * (bit 0), pfb_id (bits 4-5), mgt_id (bits 6-8), mgt_bank (bits 9-13); word
+ * three: mgt_frame (bits 0-8), mgt_group (bits 9-10), mgt_channel (bits
+ * 11-15); 256 sample bytes; the XOR of the 128 data words.  Words are most
+ * significant byte first.  The bit positions and mgt_frame's 9-bit width are
+ * readings: the appendix lists the fields but not their placement, and gives
+ * mgt_frame 5 bits for the values 0-499.  Sample byte 64 f2 + k is fine
+ * channel 128 mgt_channel + 16 mgt_id + 4 mgt_group + f2 and input
+ * 64 pfb_id + k (PFB order, the X-engine's input order).
+ *
+ * d_packets: device, n_packets x 264 bytes, 4-byte aligned, any order.
+ * d_volt: device uint8 [CORR_PKT_FRAMES][CORR_PKT_CHANNELS][CORR_PKT_INPUTS],
+ * 16-byte aligned, fully written: sample t of the bank is mgt_frame t.
+ * d_seen: device scratch of CORR_PKT_SEEN_BYTES.  d_counters: device int32
+ * [CORR_PKT_COUNTERS], zeroed then filled: good packets, rejected packets by
+ * reason (header, checksum, field: mgt_bank != bank, mgt_channel >= 24,
+ * mgt_frame >= 500, or sec_tick on a packet other than the second's first),
+ * repeated slots (a repeated packet's bytes replace the earlier ones), and
+ * slots (frame, four channels, PFB) no good packet filled, whose 256 bytes
+ * are written as 0x88 (code 8 in both parts: invalid, see CORR_ZERO_INVALID).
+ * Asynchronous; allocates nothing.
+ */
+#define CORR_PKT_BYTES 264
+#define CORR_PKT_FRAMES 500
+#define CORR_PKT_CHANNELS 3072
+#define CORR_PKT_INPUTS 256
+#define CORR_PKT_SLOTS (CORR_PKT_FRAMES * (CORR_PKT_CHANNELS / 4) * 4)
+#define CORR_PKT_SEEN_BYTES (CORR_PKT_SLOTS * 4)
+#define CORR_PKT_GOOD 0
+#define CORR_PKT_BAD_HEADER 1
+#define CORR_PKT_BAD_CHECKSUM 2
+#define CORR_PKT_BAD_FIELD 3
+#define CORR_PKT_DUPLICATE 4
+#define CORR_PKT_MISSING 5
+#define CORR_PKT_COUNTERS 6
+int corr_ingest_packets(const uint8_t *d_packets, long long n_packets, int bank, uint8_t *d_volt, void *d_seen,
+                        int32_t *d_counters, void *stream);
+
 #define CORR_REMAP_MAX_DUMPS 8
 /*
  * Output remap (Appendix C, "GPU Output"): the X-engine correlates the inputs

@@ -111,6 +111,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_unpack": ([vp, c_int, c_int, c_int, vp, ctypes.c_uint, vp], c_int),
             "corr_xmac_noalloc": ([vp, c_int, c_int, c_int, vp, ctypes.c_uint, vp], c_int),
             "corr_incoherent_beam": ([vp, c_int, c_int, c_int, c_int, ctypes.c_uint, vp, vp], c_int),
+            "corr_ingest_packets": ([vp, ctypes.c_longlong, c_int, vp, vp, vp, vp], c_int),
             "corr_remap": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, vp, vp, vp], c_int),
             "corr_batch_create": ([c_int, ctypes.POINTER(ArrayDesc)], vp),
             "corr_batch_destroy": ([vp], c_int),
@@ -520,6 +521,37 @@ def incoherent_beam(volt: torch.Tensor, n_avg: int = 1, zero_invalid: bool = Fal
                                        ctypes.c_void_p(out.data_ptr()), _stream_handle(stream)),
            "corr_incoherent_beam")
     return out
+
+
+PKT_BYTES, PKT_FRAMES, PKT_CHANNELS, PKT_INPUTS = 264, 500, 3072, 256
+PKT_SLOTS = PKT_FRAMES * (PKT_CHANNELS // 4) * 4
+PKT_COUNTER_NAMES = ("good", "bad_header", "bad_checksum", "bad_field", "duplicate", "missing")
+
+
+def ingest_packets(packets: torch.Tensor, bank: int, out: torch.Tensor | None = None,
+                   seen: torch.Tensor | None = None, counters: torch.Tensor | None = None,
+                   stream=None):
+    """One bank of PFB packets (uint8 CUDA tensor [n][264]) -> the voltage block
+    uint8 [500][3072][256] and int32 counters [6] (corr_ingest_packets)."""
+    if (packets.dtype != torch.uint8 or packets.dim() != 2 or packets.shape[1] != PKT_BYTES
+            or not packets.is_contiguous() or not packets.is_cuda):
+        raise ValueError("packets must be a contiguous uint8 CUDA tensor [n][264]")
+    dev = packets.device
+    if out is None:
+        out = torch.empty((PKT_FRAMES, PKT_CHANNELS, PKT_INPUTS), dtype=torch.uint8, device=dev)
+    if seen is None:
+        seen = torch.empty(PKT_SLOTS, dtype=torch.int32, device=dev)
+    if counters is None:
+        counters = torch.empty(6, dtype=torch.int32, device=dev)
+    if tuple(out.shape) != (PKT_FRAMES, PKT_CHANNELS, PKT_INPUTS) or out.dtype != torch.uint8:
+        raise ValueError("out must be uint8 [500][3072][256]")
+    if seen.numel() * seen.element_size() < PKT_SLOTS * 4 or counters.numel() < 6 or counters.dtype != torch.int32:
+        raise ValueError("seen must hold 4 bytes per slot and counters 6 int32")
+    _check(load().corr_ingest_packets(ctypes.c_void_p(packets.data_ptr()), packets.shape[0], bank,
+                                      ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(seen.data_ptr()),
+                                      ctypes.c_void_p(counters.data_ptr()), _stream_handle(stream)),
+           "corr_ingest_packets")
+    return out, counters
 
 
 def remap(tris, nat_of_pfb: torch.Tensor | None = None, f_avg: int = 1,

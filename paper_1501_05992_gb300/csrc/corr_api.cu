@@ -679,6 +679,19 @@ int corr_incoherent_beam(const uint8_t *d_volt, int n_time, int n_chan, int n_in
     return ret(e == cudaSuccess ? CORR_OK : cuda_fail(e));
 }
 
+int corr_ingest_packets(const uint8_t *d_packets, long long n_packets, int bank, uint8_t *d_volt, void *d_seen,
+                        int32_t *d_counters, void *stream)
+{
+    if (n_packets < 0 || bank < 0 || bank > 31 || !d_volt || !d_seen || !d_counters ||
+        (n_packets > 0 && !d_packets) || (reinterpret_cast<uintptr_t>(d_packets) & 3) != 0 ||
+        (reinterpret_cast<uintptr_t>(d_volt) & 15) != 0 || (reinterpret_cast<uintptr_t>(d_seen) & 3) != 0 ||
+        (reinterpret_cast<uintptr_t>(d_counters) & 3) != 0)
+        return ret(CORR_E_ARG);
+    const cudaError_t e = launch_ingest(d_packets, n_packets, bank, d_volt, d_seen, d_counters,
+                                        static_cast<cudaStream_t>(stream));
+    return ret(e == cudaSuccess ? CORR_OK : cuda_fail(e));
+}
+
 int corr_remap(const int32_t *const *d_tri, int n_dumps, int n_inputs, int n_chan, int f_avg,
                const int32_t *d_nat_of_pfb, int32_t *d_out, void *stream)
 {

@@ -108,6 +108,11 @@ cudaError_t launch_beam(const uint8_t *volt, int n_time, int n_chan, int n, int 
 cudaError_t launch_remap(const int32_t *const *tri, int n_dumps, int n, int n_chan, int f_avg,
                          const int32_t *nat_of_pfb, int32_t *out, cudaStream_t s);
 
+// Packet ingest of one bank (see corr_ingest_packets): zeroes seen and
+// counters, scatters the good packets, marks unfilled slots invalid.
+cudaError_t launch_ingest(const uint8_t *packets, long long n_packets, int bank, uint8_t *volt, void *seen,
+                          int32_t *counters, cudaStream_t s);
+
 // Record `status` as the calling thread's last error and return it.
 int set_last_error(int status);
 
