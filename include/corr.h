@@ -391,7 +391,7 @@ int corr_ingest_packets(const uint8_t *d_packets, long long n_packets, int bank,
  * PFB's 64 carries input (k mod 4) * 16 + k div 4; PFB blocks concatenated,
  * Appendix B), which needs n_inputs % 64 == 0.  Reading: natural input a is
  * station a / 2, polarisation a % 2.  d_out: device int32
- * [n_chan / f_avg][S(S+1)/2][2][2][2], S = n_inputs / 2 (33024 complex
+ * [n_chan / f_avg][S(S+1)/2][2][2][2], 16-byte aligned, S = n_inputs / 2 (33024 complex
  * products per channel at 256 inputs).  Sums are int32: the caller keeps
  * n_dumps f_avg 128 n_time below 2^31.  A table that is not a permutation
  * gives undefined products but no out-of-bounds access.  Asynchronous.

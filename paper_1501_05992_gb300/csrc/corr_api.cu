@@ -699,8 +699,9 @@ int corr_remap(const int32_t *const *d_tri, int n_dumps, int n_inputs, int n_cha
         n_inputs % 2 != 0 || n_inputs > 8192 || n_chan < 1 || n_chan > 65535 || f_avg < 1 ||
         n_chan % f_avg != 0 || (!d_nat_of_pfb && n_inputs % 64 != 0))
         return ret(CORR_E_ARG);
+    if ((reinterpret_cast<uintptr_t>(d_out) & 15) != 0) return ret(CORR_E_ARG);
     for (int d = 0; d < n_dumps; ++d)
-        if (!d_tri[d]) return ret(CORR_E_ARG);
+        if (!d_tri[d] || (reinterpret_cast<uintptr_t>(d_tri[d]) & 7) != 0) return ret(CORR_E_ARG);
     const cudaError_t e = launch_remap(d_tri, n_dumps, n_inputs, n_chan, f_avg, d_nat_of_pfb, d_out,
                                        static_cast<cudaStream_t>(stream));
     return ret(e == cudaSuccess ? CORR_OK : cuda_fail(e));

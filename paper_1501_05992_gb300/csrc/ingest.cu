@@ -35,6 +35,12 @@ ingest_kernel(const uint32_t *__restrict__ pk, long long n_packets, int bank, ui
 {
     const int lane = threadIdx.x & 31;
     const long long warps = (long long)gridDim.x * (kIngestThreads / 32);
+    // per-warp counts (lane 0), added to the block's and then once to the
+    // global counters: one address hit by every packet would serialise
+    __shared__ int block_counts[CORR_PKT_COUNTERS];
+    if (threadIdx.x < CORR_PKT_COUNTERS) block_counts[threadIdx.x] = 0;
+    __syncthreads();
+    int mine[5] = {0, 0, 0, 0, 0};
     for (long long q = blockIdx.x * (long long)(kIngestThreads / 32) + (threadIdx.x >> 5); q < n_packets;
          q += warps) {
         const uint32_t *w = pk + q * kWords;
@@ -59,21 +65,24 @@ ingest_kernel(const uint32_t *__restrict__ pk, long long n_packets, int bank, ui
                  (tick && (bnk | chan | grp | frame) != 0))
             code = CORR_PKT_BAD_FIELD;
         if (code != CORR_PKT_GOOD) {
-            if (lane == 0) atomicAdd(counters + code, 1);
+            ++mine[code];
             continue;
         }
         const int cgroup = 32 * chan + 4 * mgt + grp;
         const long long slot = ((long long)frame * kGroups + cgroup) * 4 + pfb;
-        if (lane == 0) {
-            if (atomicExch(seen + slot, 1u) != 0u) atomicAdd(counters + CORR_PKT_DUPLICATE, 1);
-            atomicAdd(counters + CORR_PKT_GOOD, 1);
-        }
+        if (lane == 0 && atomicExch(seen + slot, 1u) != 0u) ++mine[CORR_PKT_DUPLICATE];
+        ++mine[CORR_PKT_GOOD];
         // data word l holds channel f2 = l / 16, inputs 64 pfb + 4 (l % 16) .. + 3
         const long long base = ((long long)frame * kChannels + 4 * cgroup) * kInputs + 64 * pfb + 4 * (lane & 15);
         uint32_t *o = reinterpret_cast<uint32_t *>(volt);
         o[(base + (long long)(lane >> 4) * kInputs) >> 2] = d0;
         o[(base + (long long)(2 + (lane >> 4)) * kInputs) >> 2] = d1;
     }
+    if (lane == 0)
+        for (int c = 0; c < 5; ++c)
+            if (mine[c]) atomicAdd(block_counts + c, mine[c]);
+    __syncthreads();
+    if (threadIdx.x < 5 && block_counts[threadIdx.x]) atomicAdd(counters + threadIdx.x, block_counts[threadIdx.x]);
 }
 
 // One thread per (slot, channel f2): a slot nobody filled gets 64 bytes of 0x88.
@@ -81,6 +90,7 @@ __global__ void __launch_bounds__(kIngestThreads)
 ingest_missing_kernel(uint8_t *__restrict__ volt, const uint32_t *__restrict__ seen, int *__restrict__ counters)
 {
     const long long n = (long long)CORR_PKT_SLOTS * 4;
+    int missing = 0;
     for (long long e = blockIdx.x * (long long)kIngestThreads + threadIdx.x; e < n;
          e += (long long)gridDim.x * kIngestThreads) {
         const long long slot = e >> 2;
@@ -95,8 +105,14 @@ ingest_missing_kernel(uint8_t *__restrict__ volt, const uint32_t *__restrict__ s
         dst[1] = inv;
         dst[2] = inv;
         dst[3] = inv;
-        if (f2 == 0) atomicAdd(counters + CORR_PKT_MISSING, 1);
+        if (f2 == 0) ++missing;
     }
+    __shared__ int block_missing;
+    if (threadIdx.x == 0) block_missing = 0;
+    __syncthreads();
+    if (missing) atomicAdd(&block_missing, missing);
+    __syncthreads();
+    if (threadIdx.x == 0 && block_missing) atomicAdd(counters + CORR_PKT_MISSING, block_missing);
 }
 
 }  // namespace

@@ -13,8 +13,9 @@
 //
 // with natural input a = 2 * station + pol.  V_AB with pos(A) >= pos(B) is a
 // stored triangle element; otherwise it is the conjugate of the element
-// (pos(B), pos(A)).  One thread writes one complex product; the inverse
-// permutation lives in shared memory.  The kernel is bound by HBM (reads of
+// (pos(B), pos(A)).  One thread writes the four polarisation products of one
+// station pair (32 contiguous bytes); the inverse permutation lives in shared
+// memory.  The kernel is bound by HBM (reads of
 // the triangles, which the gather touches inside one channel's triangle at a
 // time, and the coalesced writes).
 #include "internal.cuh"
@@ -54,26 +55,37 @@ remap_kernel(RemapArgs args, int n, int n_chan, int f_avg, const int32_t *__rest
     const int S = n / 2;
     const long long Q = n_pairs(S);
     const int g = blockIdx.y;
-    for (long long o = blockIdx.x * (long long)blockDim.x + threadIdx.x; o < Q * 4;
-         o += (long long)gridDim.x * blockDim.x) {
-        const long long q = o >> 2;
-        const int p1 = int(o >> 1) & 1, p2 = int(o) & 1;
+    // one thread per station pair: its four polarisation products are 32
+    // contiguous output bytes
+    for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Q;
+         q += (long long)gridDim.x * blockDim.x) {
         int s1 = int((sqrtf(8.0f * float(q) + 1.0f) - 1.0f) * 0.5f);
         while (n_pairs(s1 + 1) <= q) ++s1;
         while (n_pairs(s1) > q) --s1;
         const int s2 = int(q - n_pairs(s1));
-        const int i = pos[2 * s1 + p1], j = pos[2 * s2 + p2];
-        const bool conj = i < j;
-        const long long k = conj ? n_pairs(j) + i : n_pairs(i) + j;
-        int re = 0, im = 0;
+        long long k[4];
+        bool conj[4];
+#pragma unroll
+        for (int pp = 0; pp < 4; ++pp) {
+            const int i = pos[2 * s1 + (pp >> 1)], j = pos[2 * s2 + (pp & 1)];
+            conj[pp] = i < j;
+            k[pp] = conj[pp] ? n_pairs(j) + i : n_pairs(i) + j;
+        }
+        int re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
         for (int d = 0; d < args.n_dumps; ++d) {
             for (int f = g * f_avg; f < (g + 1) * f_avg; ++f) {
-                const int2 v = reinterpret_cast<const int2 *>(args.tri[d])[(long long)f * P + k];
-                re += v.x;
-                im += v.y;
+                const int2 *tri = reinterpret_cast<const int2 *>(args.tri[d]) + (long long)f * P;
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) {
+                    const int2 v = __ldg(tri + k[pp]);
+                    re[pp] += v.x;
+                    im[pp] += v.y;
+                }
             }
         }
-        reinterpret_cast<int2 *>(out)[(long long)g * Q * 4 + o] = make_int2(re, conj ? -im : im);
+        int4 *o = reinterpret_cast<int4 *>(out) + ((long long)g * Q + q) * 2;
+        o[0] = make_int4(re[0], conj[0] ? -im[0] : im[0], re[1], conj[1] ? -im[1] : im[1]);
+        o[1] = make_int4(re[2], conj[2] ? -im[2] : im[2], re[3], conj[3] ? -im[3] : im[3]);
     }
 }
 
@@ -86,8 +98,8 @@ cudaError_t launch_remap(const int32_t *const *tri, int n_dumps, int n, int n_ch
     RemapArgs args{};
     for (int d = 0; d < n_dumps; ++d) args.tri[d] = tri[d];
     args.n_dumps = n_dumps;
-    const long long Q4 = n_pairs(n / 2) * 4;
-    const long long want = (Q4 + kRemapThreads - 1) / kRemapThreads;
+    const long long Q = n_pairs(n / 2);
+    const long long want = (Q + kRemapThreads - 1) / kRemapThreads;
     const int bx = int(want < 4096 ? want : 4096);
     const dim3 grid(unsigned(bx), unsigned(n_chan / f_avg));
     remap_kernel<<<grid, kRemapThreads, size_t(n) * sizeof(int), s>>>(args, n, n_chan, f_avg, nat_of_pfb, out);
