@@ -40,6 +40,8 @@ WORKLOADS = {
     "full_band": ([(256, 3072, 5000)], 16, 1503),
     "coarse_channel": ([(256, 128, 5000)], 1, 1502),
     "uneven_batch": ([(128, 1536, 2000), (256, 3072, 5000), (1024, 512, 10000)], 1, 1504),
+    # one 50 ms bank of the full band (the packet ingest's unit): a small case for profiles
+    "bank": ([(256, 3072, 500)], 1, 1506),
 }
 
 
