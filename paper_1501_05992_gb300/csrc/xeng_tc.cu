@@ -35,10 +35,12 @@
 //   warp 0     TMA producer: packed bytes [64 samples][128 inputs] per tile,
 //              with L2 prefetch of the tiles kPrefetchStages stages ahead
 //   warp 1     TMEM allocator and single-thread MMA issuer
-//   warps 2-17 converters: packed bytes -> E4M3 planes (+ per-input sums), as
-//              two teams of 8 warps that take alternate 64-sample stages (a
-//              warp's barrier waits and arrivals cost about as much as its
-//              conversion work, so a team owning whole stages halves that cost)
+//   warps 2-16, 22  converters: packed bytes -> E4M3 planes (+ per-input
+//              sums), as two teams of 8 warps that take alternate 64-sample
+//              stages (a warp's barrier waits and arrivals cost about as much as
+//              its conversion work, so a team owning whole stages halves that
+//              cost); warp 17 is left idle so that the MMA warp's scheduler
+//              (warps 1, 5, 9, ... share one) serves one converter warp fewer
 //   warps 18-21 epilogue: TMEM -> int32, corrections, packed-triangle store
 // Accumulators are double-buffered in TMEM (2 x 256 columns) so the epilogue
 // of one item overlaps the main loop of the next.  Every wait is bounded: on
@@ -77,7 +79,7 @@ constexpr int kTeams = 2, kTeamWarps = kConvWarps / kTeams;   // converter teams
 // use g - 2 kPackedStages.  (Plane slots are waited on by the in-order MMA
 // issuer, and their "empty" waits are ordered by it, so any count works.)
 static_assert(kPackedStages % kTeams == 0, "packed slots must be team-exclusive");
-constexpr int kThreads = (2 + kConvWarps + kEpiWarps) * 32;   // 704
+constexpr int kThreads = (2 + kConvWarps + kEpiWarps + 1) * 32;   // 736: warp 22 converts, warp 17 idles
 constexpr int kFirstConvWarp = 2, kFirstEpiWarp = 2 + kConvWarps;
 constexpr int kTmemCols = 512;               // 2 accumulator buffers x (128 Re + 128 Im)
 constexpr long long kDefaultWaitLimit = 1LL << 31;  // clock64 cycles (about 1 s)
@@ -152,6 +154,21 @@ __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity)
     return done != 0;
 }
 
+// As mbar_try, but a thread whose phase is not complete may be suspended for
+// up to 1 ms (it resumes as soon as the phase completes), so bounded waits
+// poll rarely instead of spinning.
+__device__ __forceinline__ bool mbar_try_sleep(uint32_t bar, uint32_t parity)
+{
+    uint32_t done;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(done)
+        : "r"(bar), "r"(parity), "n"(1000000)
+        : "memory");
+    return done != 0;
+}
+
 // Bounded wait.  Returns false on timeout or if another role aborted.
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatile int *abort,
                                           DeviceStatus *status, int where, long long limit)
@@ -159,7 +176,7 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity, volatil
     if (mbar_try(bar, parity)) return true;
     const long long t0 = clock64();
     while (true) {
-        if (mbar_try(bar, parity)) return true;
+        if (mbar_try_sleep(bar, parity)) return true;
         if (*abort) return false;
         if (clock64() - t0 > limit) {
             *abort = 1;
@@ -487,7 +504,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             while (!mbar_try(bar_drain, 0) && clock64() - t0 < p.wait_limit) {
             }
         }
-    } else if (warp < kFirstEpiWarp) {
+    } else if ((warp >= 2 && warp <= 16) || warp == 22) {
         // ----------------------------------------------------- converters --
         // Two teams of kTeamWarps warps; team t converts the stages g (counted
         // over all items of this CTA) with g % 2 == t, so each warp spends its
@@ -496,8 +513,9 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
         // stages, so its per-input sums cover 16 inputs and stay in registers:
         //   off-diagonal item: q < 16 -> J tile, q >= 16 -> I tile, rows (q & 15) + 16k, k < 4
         //   diagonal item:     J tile, rows q + 32k, k < 2
-        const int team = (warp - kFirstConvWarp) / kTeamWarps;
-        const int u = threadIdx.x - (kFirstConvWarp + team * kTeamWarps) * 32;   // 0..255
+        const int ci = warp <= 16 ? warp - 2 : 15;
+        const int team = ci / kTeamWarps;
+        const int u = (ci % kTeamWarps) * 32 + lane;   // 0..255
         const int c = u & 7, q = u >> 3;                                         // q 0..31
         uint32_t g0 = 0;                        // global index of the item's first stage
         int local = 0;
@@ -617,7 +635,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_sums_full(buf));
         }
-    } else {
+    } else if (warp >= kFirstEpiWarp && warp < kFirstEpiWarp + kEpiWarps) {
         // ------------------------------------------------------- epilogue --
         const int q = warp & 3;                      // TMEM lane quarter of this warp
         uint32_t aphase = 0;                          // bit b: phase of buffer b
