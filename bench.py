@@ -34,6 +34,11 @@ sys.path.insert(0, ROOT)
 METRIC = "Correlator CMAC/s and ×real-time, 256 inputs×3072 ch; TC vs CUDA-core, bit-exact"
 UNIT = "CMAC/s"
 SAMPLE_RATE_HZ = 1.0e4            # 10 kHz fine channels: one sample per channel per 100 us
+# register-resident probe rates on GB300 at 2070 MHz (used as the roofline of
+# the two non-tcgen05 paths): dp4a issue rate per SM per clock, and mma.sync
+# m16n8k32 s8 throughput
+DP4A_PER_SM_CLOCK = 64
+MMA_S8_TOPS_MEASURED = 158.0
 
 WORKLOADS = {
     # name: arrays [(n_inputs, n_chan, samples per integration)], integrations per step, seed
@@ -278,17 +283,19 @@ def roofline_for(path, ops_per_launch, avg_ms, peaks, src, sm_count):
                 "frac": achieved / peak,
                 "peak_note": f"fp8 dense = 2 x bf16 sustained ({src}); ops = 8 per useful CMAC"}
     if path == "mma_i8":
-        peak = peaks["bf16_tflops_sustained"] * 2.0
+        # int8 tensor rates on this part are far below 2 x bf16; the peak is
+        # the measured rate of back-to-back mma.sync m16n8k32 s8 in registers
+        peak = MMA_S8_TOPS_MEASURED
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TOPS",
                 "frac": achieved / peak,
-                "peak_note": f"int8 taken at the nominal 2 x bf16 sustained ({src}); "
-                             "ops = 8 per useful CMAC"}
-    # dp4a: one 4-way int8 dot product per lane per clock (upper bound)
-    peak = sm_count * 128 * 4 * 2 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+                "peak_note": "measured mma.sync s8 peak (register-resident probe); ops = 8 per useful CMAC"}
+    # dp4a: the integer pipe issues 16 lanes per scheduler per clock (64 per
+    # SM, measured with a register-resident probe); 8 ops per dp4a
+    peak = sm_count * DP4A_PER_SM_CLOCK * 8 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOPS",
             "frac": achieved / peak,
-            "peak_note": f"{sm_count} SMs x 128 lanes x 1 dp4a (8 ops) per clock at "
-                         f"{peaks.get('sm_max_mhz', 2070.0):.0f} MHz"}
+            "peak_note": f"{sm_count} SMs x {DP4A_PER_SM_CLOCK} dp4a per clock (measured issue rate) x 8 ops "
+                         f"at {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"}
 
 
 def _time_ms(fn, stream, reps=5):
