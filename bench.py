@@ -192,6 +192,24 @@ def oracle_sample(volt_host_slab, seconds_budget: float):
     return cmac / dt, oracle.threads(), desc
 
 
+def oracle_single_core(volt_host_slab):
+    """The oracle on one core, over one channel of the same slab: (CMAC/s, sample str)."""
+    import numpy as np
+    import oracle
+    T, F, N = volt_host_slab.shape
+    P = N * (N + 1) // 2
+    before = oracle.threads()
+    oracle.set_threads(1)
+    try:
+        one = np.ascontiguousarray(volt_host_slab[:, :1, :])
+        t0 = time.perf_counter()
+        oracle.xmac(one)
+        dt = time.perf_counter() - t0
+    finally:
+        oracle.set_threads(before)
+    return P * T / dt, f"1 channel x {T} samples x {N} inputs on one core ({dt:.1f} s)"
+
+
 def host_sample_slab(n_inputs, n_chan, n_time, seed, channels):
     from synth import voltgen as vg
     p = vg.gauss3_params(seed, n_inputs, n_chan)
@@ -543,7 +561,9 @@ def run_ours(args, world, rank, local):
         n, f, t = arrays[0]
         slab = volts[0][:t, :min(f, 256)].cpu().numpy()
         rate, cores, desc = oracle_sample(slab, args.cpu_seconds)
-        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc}
+        one_rate, one_desc = oracle_single_core(slab)
+        cpu = {"value": rate, "unit": UNIT, "cores": cores, "kind": "oracle", "sample": desc,
+               "single_core": {"value": one_rate, "unit": UNIT, "sample": one_desc}}
 
     if rank == 0:
         line = {

@@ -84,6 +84,8 @@ class OracleLib:
         lib.oracle_remap.restype = c_int
         lib.oracle_ingest.argtypes = [u8p, ctypes.c_int64, c_int, u8p, i64p]
         lib.oracle_ingest.restype = c_int
+        lib.oracle_set_threads.argtypes = [c_int]
+        lib.oracle_set_threads.restype = c_int
         lib.oracle_threads.argtypes = []
         lib.oracle_threads.restype = c_int
         self.lib = lib
@@ -176,6 +178,10 @@ class OracleLib:
             raise ValueError("oracle_ingest: bad arguments")
         return volt, counters
 
+    def set_threads(self, n: int) -> int:
+        """Set the OpenMP threads of the triangle routine; returns the count in effect."""
+        return int(self.lib.oracle_set_threads(int(n)))
+
     def threads(self) -> int:
         """OpenMP threads the triangle routine uses."""
         return int(self.lib.oracle_threads())
@@ -225,6 +231,10 @@ def pfb_order(n_inputs: int) -> np.ndarray:
         raise ValueError("the PFB order is defined for whole PFBs of 64 inputs")
     k = np.arange(n_inputs)
     return ((k // 64) * 64 + (k % 64 % 4) * 16 + (k % 64) // 4).astype(np.int32)
+
+
+def set_threads(n: int) -> int:
+    return default().set_threads(n)
 
 
 def threads() -> int:

@@ -381,6 +381,20 @@ int oracle_ingest(const uint8_t *pk, int64_t n_packets, int bank, uint8_t *volt,
     return 0;
 }
 
+/* Set the number of OpenMP threads of the triangle routine (n >= 1); returns
+ * the number in effect afterwards. */
+int oracle_set_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1)
+        omp_set_num_threads(n);
+    return omp_get_max_threads();
+#else
+    (void)n;
+    return 1;
+#endif
+}
+
 /* Number of OpenMP threads the triangle routine would use (1 without OpenMP). */
 int oracle_threads(void)
 {

@@ -17,9 +17,22 @@
 #include <utility>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "internal.cuh"
 
 using namespace corr;
+
+namespace {
+// NVTX range around a public call (free when no profiler is attached): the
+// unpack, X-engine and dump launches show up under the call that made them.
+struct Range {
+    explicit Range(const char *name) { nvtxRangePushA(name); }
+    ~Range() { nvtxRangePop(); }
+    Range(const Range &) = delete;
+    Range &operator=(const Range &) = delete;
+};
+}  // namespace
 
 struct corr_ctx {
     int n = 0, f = 0, t_max = 0;
@@ -466,6 +479,7 @@ int corr_bind_workspace(corr_ctx *c, void *d_ws, size_t bytes)
 
 int corr_accumulate(corr_ctx *c, const uint8_t *d_volt, int n_time, void *stream)
 {
+    Range nvtx_range("corr_accumulate");
     if (!c || n_time < 0) return ret(CORR_E_ARG);
     if (!c->ws) return ret(CORR_E_STATE);
     if (n_time == 0) return ret(CORR_OK);
@@ -479,6 +493,7 @@ int corr_accumulate(corr_ctx *c, const uint8_t *d_volt, int n_time, void *stream
 
 int corr_dump(corr_ctx *c, int32_t *d_vis, void *stream)
 {
+    Range nvtx_range("corr_dump");
     if (!c || !d_vis) return ret(CORR_E_ARG);
     if (!c->ws) return ret(CORR_E_STATE);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -494,6 +509,7 @@ int corr_dump(corr_ctx *c, int32_t *d_vis, void *stream)
 
 int corr_integrate(corr_ctx *c, const uint8_t *d_volt, int n_time, int32_t *d_vis, void *stream)
 {
+    Range nvtx_range("corr_integrate");
     if (!c || n_time < 0 || !d_vis) return ret(CORR_E_ARG);
     if (!c->ws) return ret(CORR_E_STATE);
     if (n_time > c->t_max) return ret(CORR_E_OVERFLOW);
@@ -521,6 +537,7 @@ long long corr_samples(const corr_ctx *c)
 
 int corr_accumulate_host(corr_ctx *c, const uint8_t *h_volt, int n_time, void *stream)
 {
+    Range nvtx_range("corr_accumulate_host");
     if (!c || n_time < 0) return ret(CORR_E_ARG);
     if (!c->ws) return ret(CORR_E_STATE);
     if (n_time == 0) return ret(CORR_OK);
@@ -553,6 +570,7 @@ int corr_accumulate_host(corr_ctx *c, const uint8_t *h_volt, int n_time, void *s
 
 int corr_dump_host(corr_ctx *c, int32_t *h_vis, void *stream)
 {
+    Range nvtx_range("corr_dump_host");
     if (!c || !h_vis) return ret(CORR_E_ARG);
     if (!c->ws) return ret(CORR_E_STATE);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
@@ -668,6 +686,7 @@ int corr_set_state(corr_ctx *c, const void *h_buf, size_t bytes, void *stream)
 int corr_incoherent_beam(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs, int n_avg,
                          unsigned flags, int32_t *d_beam, void *stream)
 {
+    Range nvtx_range("corr_incoherent_beam");
     if (n_time < 0 || n_chan < 1 || n_chan > (1 << 24) || n_inputs < 1 || n_inputs > 65536 || n_avg < 1 ||
         n_time % n_avg != 0 || (long long)n_avg * n_inputs * 128LL >= (1LL << 31) ||
         (flags & ~CORR_ZERO_INVALID))
@@ -682,6 +701,7 @@ int corr_incoherent_beam(const uint8_t *d_volt, int n_time, int n_chan, int n_in
 int corr_ingest_packets(const uint8_t *d_packets, long long n_packets, int bank, uint8_t *d_volt, void *d_seen,
                         int32_t *d_counters, void *stream)
 {
+    Range nvtx_range("corr_ingest_packets");
     if (n_packets < 0 || bank < 0 || bank > 31 || !d_volt || !d_seen || !d_counters ||
         (n_packets > 0 && !d_packets) || (reinterpret_cast<uintptr_t>(d_packets) & 3) != 0 ||
         (reinterpret_cast<uintptr_t>(d_volt) & 15) != 0 || (reinterpret_cast<uintptr_t>(d_seen) & 3) != 0 ||
@@ -695,6 +715,7 @@ int corr_ingest_packets(const uint8_t *d_packets, long long n_packets, int bank,
 int corr_remap(const int32_t *const *d_tri, int n_dumps, int n_inputs, int n_chan, int f_avg,
                const int32_t *d_nat_of_pfb, int32_t *d_out, void *stream)
 {
+    Range nvtx_range("corr_remap");
     if (!d_tri || !d_out || n_dumps < 1 || n_dumps > CORR_REMAP_MAX_DUMPS || n_inputs < 2 ||
         n_inputs % 2 != 0 || n_inputs > 8192 || n_chan < 1 || n_chan > 65535 || f_avg < 1 ||
         n_chan % f_avg != 0 || (!d_nat_of_pfb && n_inputs % 64 != 0))
@@ -710,6 +731,7 @@ int corr_remap(const int32_t *const *d_tri, int n_dumps, int n_inputs, int n_cha
 int corr_unpack(const uint8_t *d_volt, int n_time, int n_chan, int n_inputs, int8_t *d_out,
                 unsigned flags, void *stream)
 {
+    Range nvtx_range("corr_unpack");
     if (n_time < 0 || n_chan < 1 || n_inputs < 1 || n_chan > 65535 ||
         (flags & ~CORR_ZERO_INVALID))
         return ret(CORR_E_ARG);
@@ -904,6 +926,7 @@ int batch_correlate(corr_batch *b, const uint8_t *const *d_volt, const int *n_ti
 int corr_batch_accumulate(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
                           void *stream)
 {
+    Range nvtx_range("corr_batch_accumulate");
     if (!b || !d_volt || !n_time) return ret(CORR_E_ARG);
     if (!b->bound) return ret(CORR_E_STATE);
     // every check before anything is enqueued
@@ -918,6 +941,7 @@ int corr_batch_accumulate(corr_batch *b, const uint8_t *const *d_volt, const int
 int corr_batch_integrate(corr_batch *b, const uint8_t *const *d_volt, const int *n_time,
                          int32_t *const *d_vis, void *stream)
 {
+    Range nvtx_range("corr_batch_integrate");
     if (!b || !d_volt || !n_time || !d_vis) return ret(CORR_E_ARG);
     if (!b->bound) return ret(CORR_E_STATE);
     for (int a = 0; a < b->n; ++a) {
@@ -939,6 +963,7 @@ int corr_batch_integrate(corr_batch *b, const uint8_t *const *d_volt, const int 
 
 int corr_batch_dump(corr_batch *b, int32_t *const *d_vis, void *stream)
 {
+    Range nvtx_range("corr_batch_dump");
     if (!b || !d_vis) return ret(CORR_E_ARG);
     if (!b->bound) return ret(CORR_E_STATE);
     for (int a = 0; a < b->n; ++a) {
@@ -994,6 +1019,7 @@ int corr_batch_graph_capture(corr_batch *b, const uint8_t *const *d_volt, const 
 
 int corr_graph_launch(void *graph_exec, void *stream)
 {
+    Range nvtx_range("corr_graph_launch");
     if (!graph_exec) return ret(CORR_E_ARG);
     if (cudaGraphLaunch(static_cast<cudaGraphExec_t>(graph_exec), static_cast<cudaStream_t>(stream)) !=
         cudaSuccess) {
