@@ -31,6 +31,13 @@
 // Operands are MN-major (inputs contiguous, the natural [t][n] order of the
 // voltages), 128-byte swizzled, so no transpose is ever needed.
 //
+// Work items: per channel, a diagonal tile (J, J) and the tile below it
+// (J + 1, J) form one "pair" item, since both multiply by the J tile's planes:
+// the pair converts the two tiles once and issues both MMA chains, into the
+// two TMEM accumulators.  The other tiles (I >= J + 2) are single items, and
+// the last J tile's diagonal is a single item too (for 256 inputs: one pair
+// and one diagonal item per channel, where single items would make three).
+//
 // Pipeline (persistent, one CTA per SM, work item = (channel, I tile, J tile)):
 //   warp 0     TMA producer: packed bytes [64 samples][128 inputs] per tile,
 //              with L2 prefetch of the tiles kPrefetchStages stages ahead
@@ -42,8 +49,10 @@
 //              cost); warp 17 is left idle so that the MMA warp's scheduler
 //              (warps 1, 5, 9, ... share one) serves one converter warp fewer
 //   warps 18-21 epilogue: TMEM -> int32, corrections, packed-triangle store
-// Accumulators are double-buffered in TMEM (2 x 256 columns) so the epilogue
-// of one item overlaps the main loop of the next.  Every wait is bounded: on
+// TMEM holds two accumulators (2 x 256 columns).  A single item takes the
+// next one in turn, so its epilogue overlaps the main loop of the next item; a
+// pair item takes both, its diagonal part in the one that is released first.
+// Every wait is bounded: on
 // a timeout the kernel records CORR_E_TIMEOUT, drains its own copies and MMAs,
 // frees TMEM and returns.
 #include <cuda.h>
@@ -81,7 +90,7 @@ constexpr int kTeams = 2, kTeamWarps = kConvWarps / kTeams;   // converter teams
 static_assert(kPackedStages % kTeams == 0, "packed slots must be team-exclusive");
 constexpr int kThreads = (2 + kConvWarps + kEpiWarps + 1) * 32;   // 736: warp 22 converts, warp 17 idles
 constexpr int kFirstConvWarp = 2, kFirstEpiWarp = 2 + kConvWarps;
-constexpr int kTmemCols = 512;               // 2 accumulator buffers x (128 Re + 128 Im)
+constexpr int kTmemCols = 512;               // 2 accumulator slots x (128 Re + 128 Im)
 constexpr long long kDefaultWaitLimit = 1LL << 31;  // clock64 cycles (about 1 s)
 
 // shared-memory map (offsets from a 1024-aligned base)
@@ -98,8 +107,8 @@ constexpr int kSmemBytes = kSmMisc + 64 + 1024;                                 
 constexpr uint32_t kIdesc = (1u << 4) | (0u << 7) | (0u << 10) | (1u << 15) | (1u << 16) |
                             ((256u >> 3) << 17) | ((128u >> 4) << 24);
 
-// One array of a launch.  Items (channel, I tile, J tile) of array a are
-// numbered item_begin .. item_begin + n_chan * per_chan - 1; the host orders
+// One array of a launch.  The work items of array a are numbered
+// item_begin .. item_begin + n_chan * per_chan - 1; the host orders
 // the arrays by decreasing n_stages so that a CTA's last items are its
 // shortest (a static longest-first schedule).
 struct ArrayParams {
@@ -300,18 +309,34 @@ __device__ __forceinline__ void named_sync(int id, int threads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-__device__ __forceinline__ void item_tiles(int p, int &I, int &J)
+// Work items of one channel, for n_tiles tiles of 128 inputs: for each J tile,
+// a pair item covering the tile pairs (J, J) and (J + 1, J) (they share the J
+// tile's planes, so one conversion feeds both, into two accumulators), then
+// the off-diagonal items (I, J) for I >= J + 2; the last J tile has only its
+// diagonal item.  n_tiles (n_tiles + 1) / 2 - (n_tiles - 1) items per channel.
+enum ItemKind { kDiagItem = 0, kOffItem = 1, kPairItem = 2 };
+
+__host__ __device__ __forceinline__ int items_per_channel(int n_tiles) { return n_tiles * (n_tiles + 1) / 2 - (n_tiles - 1); }
+
+__device__ __forceinline__ void item_tiles(int k, int n_tiles, int &I, int &J, int &kind)
 {
-    int i = int((sqrtf(8.0f * float(p) + 1.0f) - 1.0f) * 0.5f);
-    while ((i + 1) * (i + 2) / 2 <= p) ++i;
-    while (i * (i + 1) / 2 > p) --i;
-    I = i;
-    J = p - i * (i + 1) / 2;
+    for (J = 0; J < n_tiles; ++J) {
+        const int cnt = J + 1 < n_tiles ? n_tiles - J - 1 : 1;
+        if (k < cnt) break;
+        k -= cnt;
+    }
+    if (J + 1 < n_tiles) {
+        I = J + 1 + k;
+        kind = k == 0 ? kPairItem : kOffItem;
+    } else {
+        I = J;
+        kind = kDiagItem;
+    }
 }
 
 struct Item {
-    int a, f, I, J;
-    bool diag;
+    int a, f, I, J, kind;
+    bool diag;      // the producer and the converters see a pair item as the off-diagonal (J + 1, J)
 };
 
 __device__ __forceinline__ Item decode_item(const Params &p, int item)
@@ -322,8 +347,14 @@ __device__ __forceinline__ Item decode_item(const Params &p, int item)
     const ArrayParams &A = p.a[it.a];
     const int local = item - A.item_begin;
     it.f = local / A.per_chan;
-    item_tiles(local - it.f * A.per_chan, it.I, it.J);
-    it.diag = it.I == it.J;
+    // The CTAs take items with a stride of gridDim.x; rotate the kinds of a
+    // channel by the stride round of its first item, so that each CTA meets
+    // every kind in turn rather than one kind throughout (a bijection within
+    // every channel, so all roles of the CTA agree on it).
+    const int k = local - it.f * A.per_chan;
+    const int round = (A.item_begin + it.f * A.per_chan) / int(gridDim.x);
+    item_tiles((k + round) % A.per_chan, A.n_tiles, it.I, it.J, it.kind);
+    it.diag = it.kind == kDiagItem;
     return it;
 }
 
@@ -455,26 +486,36 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             const uint64_t desc_planes = smem_desc(sbase + kSmPlanes, kPlaneBytes, 1024);
             int stage = 0;
             uint32_t phase = 0;
-            uint32_t acc_phase = 0;                  // bit b: phase of accumulator buffer b
-            int local = 0;
+            // TMEM holds two accumulators ("slots"); a pair item fills both (its
+            // diagonal part first), any other item the next one
+            uint32_t slot_phase = 0;                 // bit s: phase of slot s
+            int next_slot = 0;
             bool ok = true;
-            for (int item = first_item; ok && item < p.n_items; item += item_step, ++local) {
+            for (int item = first_item; ok && item < p.n_items; item += item_step) {
                 const Item it = decode_item(p, item);
                 const int n_stages = p.a[it.a].n_stages;
-                const bool diag = it.diag;
-                const int buf = local & 1;
-                if (!mbar_wait(bar_acc_empty(buf), ((acc_phase >> buf) & 1u) ^ 1u, abort, p.status, 2, p.wait_limit)) {
-                    ok = false;
-                    break;
+                const bool pair = it.kind == kPairItem;
+                const int s0 = next_slot, s1 = next_slot ^ 1;
+                if (!pair) next_slot ^= 1;
+                const int n_parts = pair ? 2 : 1;
+                for (int part = 0; ok && part < n_parts; ++part) {
+                    const int sl = part == 0 ? s0 : s1;
+                    if (!mbar_wait(bar_acc_empty(sl), ((slot_phase >> sl) & 1u) ^ 1u, abort, p.status, 2,
+                                   p.wait_limit))
+                        ok = false;
+                    slot_phase ^= 1u << sl;
                 }
-                acc_phase ^= 1u << buf;
+                if (!ok) break;
                 fence_after();
-                const uint32_t d_tmem = tmem + uint32_t(buf * 256);
                 // descriptors differ only in the start-address field (bits 0-13,
                 // address >> 4, below 2^14 for any shared address): build the
-                // plane-stage-0 descriptors once and add offsets
-                const uint64_t dR = desc_planes + uint64_t((diag ? kOffRJ : kOffRI) >> 4);
-                const uint64_t dM = desc_planes + uint64_t((diag ? kOffMJ : kOffMI) >> 4);
+                // plane-stage-0 descriptors once and add offsets.  Part 0 of a pair
+                // (and a diagonal item) multiplies the J planes by themselves.
+                const bool a_is_j = it.kind != kOffItem;
+                const uint32_t t0 = tmem + uint32_t(s0 * 256), t1 = tmem + uint32_t(s1 * 256);
+                const uint64_t dR0 = desc_planes + uint64_t((a_is_j ? kOffRJ : kOffRI) >> 4);
+                const uint64_t dM0 = desc_planes + uint64_t((a_is_j ? kOffMJ : kOffMI) >> 4);
+                const uint64_t dR1 = desc_planes + uint64_t(kOffRI >> 4), dM1 = desc_planes + uint64_t(kOffMI >> 4);
                 const uint64_t dRJ = desc_planes + uint64_t(kOffRJ >> 4), dMJ = desc_planes + uint64_t(kOffMJ >> 4);
                 uint32_t accum = 0;
                 for (int s = 0; s < n_stages; ++s) {
@@ -484,10 +525,16 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                     }
                     fence_after();
                     const uint64_t so = uint64_t((stage * kPlaneStageBytes) >> 4);
-                    mma_f8(d_tmem, dR + so, dRJ + so, accum);
-                    mma_f8(d_tmem, dM + so, dMJ + so, 1);
-                    mma_f8(d_tmem, dR + so + 256u, dRJ + so + 256u, 1);
-                    mma_f8(d_tmem, dM + so + 256u, dMJ + so + 256u, 1);
+                    mma_f8(t0, dR0 + so, dRJ + so, accum);
+                    mma_f8(t0, dM0 + so, dMJ + so, 1);
+                    mma_f8(t0, dR0 + so + 256u, dRJ + so + 256u, 1);
+                    mma_f8(t0, dM0 + so + 256u, dMJ + so + 256u, 1);
+                    if (pair) {
+                        mma_f8(t1, dR1 + so, dRJ + so, accum);
+                        mma_f8(t1, dM1 + so, dMJ + so, 1);
+                        mma_f8(t1, dR1 + so + 256u, dRJ + so + 256u, 1);
+                        mma_f8(t1, dM1 + so + 256u, dMJ + so + 256u, 1);
+                    }
                     accum = 1;
                     mma_commit(bar_plane_empty(stage));
                     if (++stage == kPlaneStages) {
@@ -496,7 +543,8 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                     }
                 }
                 if (!ok) break;
-                mma_commit(bar_acc_full(buf));
+                mma_commit(bar_acc_full(s0));
+                if (pair) mma_commit(bar_acc_full(s1));
             }
             // drain all MMAs issued by this thread before TMEM is released
             mma_commit(bar_drain);
@@ -638,7 +686,8 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
     } else if (warp >= kFirstEpiWarp && warp < kFirstEpiWarp + kEpiWarps) {
         // ------------------------------------------------------- epilogue --
         const int q = warp & 3;                      // TMEM lane quarter of this warp
-        uint32_t aphase = 0;                          // bit b: phase of buffer b
+        uint32_t slot_phase = 0;                      // bit s: phase of TMEM slot s (same rule as the MMA warp)
+        int next_slot = 0;
         int local = 0;
         bool ok = true;
         if (p.inject_stall) {
@@ -658,75 +707,87 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             int32_t *const acc = p.a[it.a].acc;
             const long long P = n_pairs(n_in);
             const int T_eff = p.a[it.a].n_stages * kTc;
-            const int f = it.f, I = it.I, J = it.J;
-            const bool diag = it.diag;
-            const int buf = local & 1;
-            // the four epilogue warps decide together whether to go on, so that
-            // none of them is ever left waiting at a named barrier
-            const uint32_t ph = (aphase >> buf) & 1u;
-            const bool mine = warp_wait(bar_acc_full(buf), ph, abort, p.status, 7, lane, p.wait_limit, 256) &&
-                              warp_wait(bar_sums_full(buf), ph, abort, p.status, 8, lane, p.wait_limit, 64);
-            if (lane == 0) epi_ok[q] = mine ? 1 : 0;
-            named_sync(2, kEpiWarps * 32);
-            ok = epi_ok[0] && epi_ok[1] && epi_ok[2] && epi_ok[3];
-            named_sync(2, kEpiWarps * 32);
-            if (!ok) break;
-            aphase ^= 1u << buf;
-            fence_after();
-            int *sb = sums + buf * (2 * 2 * kTile);
-            const int *si = sb + (diag ? 1 : 0) * 2 * kTile;     // I tile sums: [r/m][slot]
-            const int *sj = sb + 1 * 2 * kTile;                   // J tile sums
-            const int il = q * 32 + lane;
-            const int i = I * kTile + il;
-            const int Sri = si[sum_slot(il)], Smi = si[kTile + sum_slot(il)];
-            const int Ei = Sri + Smi, Di = Smi - Sri;
-            const int base_re = 128 * T_eff - 8 * Ei;
-            int32_t *out = acc + ((size_t)f * P + (size_t)i * (i + 1) / 2) * 2;
-            const uint32_t taddr = tmem + uint32_t(buf * 256) + (uint32_t(q * 32) << 16);
+            const int f = it.f, J = it.J;
+            const bool pair = it.kind == kPairItem;
+            const int s0 = next_slot, s1 = next_slot ^ 1;
+            if (!pair) next_slot ^= 1;
+            const int sbuf = local & 1;
+            int *sb = sums + sbuf * (2 * 2 * kTile);
+            const int *sj = sb + 1 * 2 * kTile;                   // J tile sums: [r/m][slot]
+            const int n_parts = pair ? 2 : 1;
+            for (int part = 0; part < n_parts; ++part) {
+                const int sl = part == 0 ? s0 : s1;
+                // part 0 of a pair, or a diagonal item: rows of the J tile
+                const bool diag = part == 0 ? it.kind != kOffItem : false;
+                const int I = diag ? J : it.I;
+                // the four epilogue warps decide together whether to go on, so that
+                // none of them is ever left waiting at a named barrier
+                bool mine = warp_wait(bar_acc_full(sl), (slot_phase >> sl) & 1u, abort, p.status, 7, lane,
+                                      p.wait_limit, 256);
+                if (part == 0)
+                    mine = mine && warp_wait(bar_sums_full(sbuf), uint32_t(local >> 1) & 1u, abort, p.status, 8,
+                                             lane, p.wait_limit, 64);
+                if (lane == 0) epi_ok[q] = mine ? 1 : 0;
+                named_sync(2, kEpiWarps * 32);
+                ok = epi_ok[0] && epi_ok[1] && epi_ok[2] && epi_ok[3];
+                named_sync(2, kEpiWarps * 32);
+                if (!ok) break;
+                slot_phase ^= 1u << sl;
+                fence_after();
+                const int *si = sb + (diag ? 1 : 0) * 2 * kTile;     // I tile sums
+                const int il = q * 32 + lane;
+                const int i = I * kTile + il;
+                const int Sri = si[sum_slot(il)], Smi = si[kTile + sum_slot(il)];
+                const int Ei = Sri + Smi, Di = Smi - Sri;
+                const int base_re = 128 * T_eff - 8 * Ei;
+                int32_t *out = acc + ((size_t)f * P + (size_t)i * (i + 1) / 2) * 2;
+                const uint32_t taddr = tmem + uint32_t(sl * 256) + (uint32_t(q * 32) << 16);
 #pragma unroll 1
-            for (int c0 = 0; c0 < kTile; c0 += 8) {
-                uint32_t vre[8], vim[8];
-                tmem_ld8(taddr + c0, vre);
-                tmem_ld8(taddr + 128 + c0, vim);
-                tmem_wait_ld();
-                // columns c0 .. c0 + 7 of row i that lie in the lower triangle
-                const int kmax = i < n_in ? min(7, i - (J * kTile + c0)) : -1;
-                if (kmax >= 0) {
-                    int2 *dst = reinterpret_cast<int2 *>(out) + (J * kTile + c0);
-                    int2 prev[8];
-                    if (!fresh) {
-                        // issue every load of the chunk before the first store
-#pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                            prev[k] = k <= kmax ? dst[k] : make_int2(0, 0);
-                    }
-#pragma unroll
-                    for (int k = 0; k < 8; ++k) {
-                        if (k > kmax) continue;
-                        const int jl = c0 + k;
-                        const int Srj = sj[sum_slot(jl)], Smj = sj[kTile + sum_slot(jl)];
-                        const int pre = __float2int_rn(__uint_as_float(vre[k]) * 262144.0f);
-                        const int pim = __float2int_rn(__uint_as_float(vim[k]) * 262144.0f);
-                        int re = pre + base_re - 8 * (Srj + Smj);
-                        int im = pim - 8 * Di + 8 * (Smj - Srj);
+                for (int c0 = 0; c0 < kTile; c0 += 8) {
+                    uint32_t vre[8], vim[8];
+                    tmem_ld8(taddr + c0, vre);
+                    tmem_ld8(taddr + 128 + c0, vim);
+                    tmem_wait_ld();
+                    // columns c0 .. c0 + 7 of row i that lie in the lower triangle
+                    const int kmax = i < n_in ? min(7, i - (J * kTile + c0)) : -1;
+                    if (kmax >= 0) {
+                        int2 *dst = reinterpret_cast<int2 *>(out) + (J * kTile + c0);
+                        int2 prev[8];
                         if (!fresh) {
-                            re += prev[k].x;
-                            im += prev[k].y;
+                            // issue every load of the chunk before the first store
+#pragma unroll
+                            for (int k = 0; k < 8; ++k)
+                                prev[k] = k <= kmax ? dst[k] : make_int2(0, 0);
                         }
-                        dst[k] = make_int2(re, im);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            if (k > kmax) continue;
+                            const int jl = c0 + k;
+                            const int Srj = sj[sum_slot(jl)], Smj = sj[kTile + sum_slot(jl)];
+                            const int pre = __float2int_rn(__uint_as_float(vre[k]) * 262144.0f);
+                            const int pim = __float2int_rn(__uint_as_float(vim[k]) * 262144.0f);
+                            int re = pre + base_re - 8 * (Srj + Smj);
+                            int im = pim - 8 * Di + 8 * (Smj - Srj);
+                            if (!fresh) {
+                                re += prev[k].x;
+                                im += prev[k].y;
+                            }
+                            dst[k] = make_int2(re, im);
+                        }
                     }
                 }
+                // this part's TMEM slot can take the next accumulation
+                fence_before();
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_acc_empty(sl));
             }
-            fence_before();
+            if (!ok) break;
             // every epilogue warp has read this item's sums: clear them for the
-            // item that reuses the buffer, then release TMEM and sums
+            // item that reuses the buffer, then release it
             named_sync(2, kEpiWarps * 32);
             for (int e = threadIdx.x - kFirstEpiWarp * 32; e < 2 * 2 * kTile; e += kEpiWarps * 32) sb[e] = 0;
             __syncwarp();
-            if (lane == 0) {
-                mbar_arrive(bar_acc_empty(buf));
-                mbar_arrive(bar_sums_empty(buf));
-            }
+            if (lane == 0) mbar_arrive(bar_sums_empty(sbuf));
         }
     }
 
@@ -855,7 +916,7 @@ cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, in
         P.n_chan = A.n_chan;
         P.nt = A.nt;
         P.n_tiles = (A.n + kTile - 1) / kTile;
-        P.per_chan = P.n_tiles * (P.n_tiles + 1) / 2;
+        P.per_chan = items_per_channel(P.n_tiles);
         P.n_stages = (A.nt + kTc - 1) / kTc;
         P.item_begin = int(items);
         P.fresh = A.fresh ? 1 : 0;
