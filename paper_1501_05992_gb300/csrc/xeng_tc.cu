@@ -37,6 +37,7 @@
 // two TMEM accumulators.  The other tiles (I >= J + 2) are single items, and
 // the last J tile's diagonal is a single item too (for 256 inputs: one pair
 // and one diagonal item per channel, where single items would make three).
+// Launches shorter than kPairMinStages stages use single items only.
 //
 // Pipeline (persistent, one CTA per SM, work item = (channel, I tile, J tile)):
 //   warp 0     TMA producer: packed bytes [64 samples][128 inputs] per tile,
@@ -91,6 +92,12 @@ static_assert(kPackedStages % kTeams == 0, "packed slots must be team-exclusive"
 constexpr int kThreads = (2 + kConvWarps + kEpiWarps + 1) * 32;   // 736: warp 22 converts, warp 17 idles
 constexpr int kFirstConvWarp = 2, kFirstEpiWarp = 2 + kConvWarps;
 constexpr int kTmemCols = 512;               // 2 accumulator slots x (128 Re + 128 Im)
+// A pair item needs both TMEM accumulators free before its first MMA, so the
+// previous item's epilogue is exposed once per pair.  On short launches that
+// costs more than the shared conversion saves, so pairs are used only from
+// this many stages on (measured crossover 32 to 64 stages for 256 and 512
+// inputs, whether the epilogue stores or adds into the output).
+constexpr int kPairMinStages = 64;
 constexpr long long kDefaultWaitLimit = 1LL << 31;  // clock64 cycles (about 1 s)
 
 // shared-memory map (offsets from a 1024-aligned base)
@@ -115,6 +122,8 @@ struct ArrayParams {
     int32_t *acc;
     int n, n_chan, nt, n_tiles, per_chan, n_stages, item_begin;
     int fresh;
+    int pairs;      // pair items in use (else one item per tile pair)
+    int rot_step;   // item rotation per stride round (see decode_item)
 };
 
 struct Params {
@@ -316,10 +325,23 @@ __device__ __forceinline__ void named_sync(int id, int threads)
 // diagonal item.  n_tiles (n_tiles + 1) / 2 - (n_tiles - 1) items per channel.
 enum ItemKind { kDiagItem = 0, kOffItem = 1, kPairItem = 2 };
 
-__host__ __device__ __forceinline__ int items_per_channel(int n_tiles) { return n_tiles * (n_tiles + 1) / 2 - (n_tiles - 1); }
-
-__device__ __forceinline__ void item_tiles(int k, int n_tiles, int &I, int &J, int &kind)
+__host__ __device__ __forceinline__ int items_per_channel(int n_tiles, bool pairs)
 {
+    return n_tiles * (n_tiles + 1) / 2 - (pairs ? n_tiles - 1 : 0);
+}
+
+__device__ __forceinline__ void item_tiles(int k, int n_tiles, bool pairs, int &I, int &J, int &kind)
+{
+    if (!pairs) {
+        // one item per tile pair, numbered row by row of the tile triangle
+        int i = int((sqrtf(8.0f * float(k) + 1.0f) - 1.0f) * 0.5f);
+        while ((i + 1) * (i + 2) / 2 <= k) ++i;
+        while (i * (i + 1) / 2 > k) --i;
+        I = i;
+        J = k - i * (i + 1) / 2;
+        kind = I == J ? kDiagItem : kOffItem;
+        return;
+    }
     for (J = 0; J < n_tiles; ++J) {
         const int cnt = J + 1 < n_tiles ? n_tiles - J - 1 : 1;
         if (k < cnt) break;
@@ -347,13 +369,17 @@ __device__ __forceinline__ Item decode_item(const Params &p, int item)
     const ArrayParams &A = p.a[it.a];
     const int local = item - A.item_begin;
     it.f = local / A.per_chan;
-    // The CTAs take items with a stride of gridDim.x; rotate the kinds of a
-    // channel by the stride round of its first item, so that each CTA meets
-    // every kind in turn rather than one kind throughout (a bijection within
-    // every channel, so all roles of the CTA agree on it).
+    // The CTAs take items with a stride of g = gridDim.x, so with c items per
+    // channel a CTA would meet the same item kind every round whenever g is a
+    // multiple of c (e.g. 2 items per channel on 152 CTAs).  In that case the
+    // host sets rot_step = 1: a channel's items rotate by one per stride round
+    // of its first item, and each CTA steps through the kinds in turn.  (When
+    // c does not divide g the stride itself moves a CTA through the kinds.)
+    // A rotation within every channel is a bijection, so all roles of the CTA
+    // agree on it.
     const int k = local - it.f * A.per_chan;
     const int round = (A.item_begin + it.f * A.per_chan) / int(gridDim.x);
-    item_tiles((k + round) % A.per_chan, A.n_tiles, it.I, it.J, it.kind);
+    item_tiles(A.rot_step ? (k + round) % A.per_chan : k, A.n_tiles, A.pairs != 0, it.I, it.J, it.kind);
     it.diag = it.kind == kDiagItem;
     return it;
 }
@@ -518,28 +544,47 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 const uint64_t dR1 = desc_planes + uint64_t(kOffRI >> 4), dM1 = desc_planes + uint64_t(kOffMI >> 4);
                 const uint64_t dRJ = desc_planes + uint64_t(kOffRJ >> 4), dMJ = desc_planes + uint64_t(kOffMJ >> 4);
                 uint32_t accum = 0;
-                for (int s = 0; s < n_stages; ++s) {
-                    if (!mbar_wait(bar_plane_full(stage), phase, abort, p.status, 3, p.wait_limit)) {
-                        ok = false;
-                        break;
-                    }
-                    fence_after();
-                    const uint64_t so = uint64_t((stage * kPlaneStageBytes) >> 4);
-                    mma_f8(t0, dR0 + so, dRJ + so, accum);
-                    mma_f8(t0, dM0 + so, dMJ + so, 1);
-                    mma_f8(t0, dR0 + so + 256u, dRJ + so + 256u, 1);
-                    mma_f8(t0, dM0 + so + 256u, dMJ + so + 256u, 1);
-                    if (pair) {
+                if (pair) {
+                    for (int s = 0; s < n_stages; ++s) {
+                        if (!mbar_wait(bar_plane_full(stage), phase, abort, p.status, 3, p.wait_limit)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint64_t so = uint64_t((stage * kPlaneStageBytes) >> 4);
+                        mma_f8(t0, dR0 + so, dRJ + so, accum);
+                        mma_f8(t0, dM0 + so, dMJ + so, 1);
+                        mma_f8(t0, dR0 + so + 256u, dRJ + so + 256u, 1);
+                        mma_f8(t0, dM0 + so + 256u, dMJ + so + 256u, 1);
                         mma_f8(t1, dR1 + so, dRJ + so, accum);
                         mma_f8(t1, dM1 + so, dMJ + so, 1);
                         mma_f8(t1, dR1 + so + 256u, dRJ + so + 256u, 1);
                         mma_f8(t1, dM1 + so + 256u, dMJ + so + 256u, 1);
+                        accum = 1;
+                        mma_commit(bar_plane_empty(stage));
+                        if (++stage == kPlaneStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
                     }
-                    accum = 1;
-                    mma_commit(bar_plane_empty(stage));
-                    if (++stage == kPlaneStages) {
-                        stage = 0;
-                        phase ^= 1u;
+                } else {
+                    for (int s = 0; s < n_stages; ++s) {
+                        if (!mbar_wait(bar_plane_full(stage), phase, abort, p.status, 3, p.wait_limit)) {
+                            ok = false;
+                            break;
+                        }
+                        fence_after();
+                        const uint64_t so = uint64_t((stage * kPlaneStageBytes) >> 4);
+                        mma_f8(t0, dR0 + so, dRJ + so, accum);
+                        mma_f8(t0, dM0 + so, dMJ + so, 1);
+                        mma_f8(t0, dR0 + so + 256u, dRJ + so + 256u, 1);
+                        mma_f8(t0, dM0 + so + 256u, dMJ + so + 256u, 1);
+                        accum = 1;
+                        mma_commit(bar_plane_empty(stage));
+                        if (++stage == kPlaneStages) {
+                            stage = 0;
+                            phase ^= 1u;
+                        }
                     }
                 }
                 if (!ok) break;
@@ -916,10 +961,11 @@ cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, in
         P.n_chan = A.n_chan;
         P.nt = A.nt;
         P.n_tiles = (A.n + kTile - 1) / kTile;
-        P.per_chan = items_per_channel(P.n_tiles);
         P.n_stages = (A.nt + kTc - 1) / kTc;
         P.item_begin = int(items);
         P.fresh = A.fresh ? 1 : 0;
+        P.pairs = P.n_tiles > 1 && P.n_stages >= kPairMinStages ? 1 : 0;
+        P.per_chan = items_per_channel(P.n_tiles, P.pairs != 0);
         items += (long long)A.n_chan * P.per_chan;
     }
     if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
@@ -929,6 +975,10 @@ cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, in
     prm.wait_limit = opt.wait_limit > 0 ? opt.wait_limit : kDefaultWaitLimit;
     prm.inject_stall = opt.inject_stall ? 1 : 0;
     const int grid = prm.n_items < g_sm_count[dev] ? prm.n_items : g_sm_count[dev];
+    for (int k = 0; k < m; ++k) {
+        ArrayParams &P = prm.a[k];
+        P.rot_step = grid % P.per_chan == 0 ? 1 : 0;
+    }
     if (zero_invalid)
         xeng_tc_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(maps, prm);
     else

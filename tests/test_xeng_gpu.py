@@ -312,3 +312,40 @@ def test_many_channels_and_tiles(path):
     volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
     want = oracle.to_int32(oracle.xmac(volt))
     assert np.array_equal(correlate(volt, path), want)
+
+
+# Work-item schemes of the tensor-core kernel: a launch of at least 64 stages
+# of 64 samples (4033+ samples) pairs each diagonal tile with the tile below
+# it; shorter launches use one item per tile pair.  These shapes cover 2, 3 and
+# 4 tiles with a ragged last tile, and each is run as one long fresh launch
+# (pairs), as a short fresh launch followed by a long accumulating one (pairs
+# adding into the output), and as launches of 1000 samples (single items).
+PAIR_SHAPES = [(130, 2, 4097), (256, 7, 4100), (272, 3, 4160), (400, 2, 4160)]
+
+
+@pytest.mark.parametrize("shape", PAIR_SHAPES, ids=lambda s: "N%d_F%d_T%d" % s)
+def test_tc_pair_and_single_items_exact(shape):
+    N, F, T = shape
+    if not path_available("tc_fp8", N):
+        pytest.skip("tc_fp8 unsupported")
+    rng = np.random.default_rng(N * 7 + F * 3 + T)
+    volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    want = oracle.to_int32(oracle.xmac(volt))
+    assert np.array_equal(correlate(volt, "tc_fp8"), want)
+    assert np.array_equal(correlate(volt, "tc_fp8", chunks=[(0, 64), (64, T)]), want)
+    short = [(a, min(a + 1000, T)) for a in range(0, T, 1000)]
+    assert np.array_equal(correlate(volt, "tc_fp8", chunks=short), want)
+
+
+def test_tc_pair_items_many_channels():
+    """More pair items than SMs, with a channel count that leaves a ragged last
+    round (256 inputs, 2 items per channel, 331 channels)."""
+    N, F, T = 256, 331, 4096
+    if not path_available("tc_fp8", N):
+        pytest.skip("tc_fp8 unsupported")
+    rng = np.random.default_rng(331)
+    volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    got = correlate(volt, "tc_fp8")
+    chans = [0, 1, 151, 152, 153, 303, 304, 330]
+    want = oracle.to_int32(oracle.xmac(np.ascontiguousarray(volt[:, chans])))
+    assert np.array_equal(got[chans], want)
