@@ -342,8 +342,26 @@ class GpuBackend:
                 d = gen.make(k * s.block_samples, s.block_samples)
                 blocks.append(d.cpu().pin_memory())
             self.pool.append(blocks)
-        self.copy_stream = torch.cuda.Stream(self.device)
-        self.compute = torch.cuda.Stream(self.device)
+        self.copy_stream = torch.cuda.Stream(self.device)     # host -> device blocks
+        self.d2h_stream = torch.cuda.Stream(self.device)      # dumps -> host, so that block
+        self.compute = torch.cuda.Stream(self.device)         # uploads never queue behind them
+        self._warm_up()
+
+    def _warm_up(self):
+        """One correlation, dump and copy of each kind before the clock starts,
+        so that the first blocks do not pay for loading kernels or for first
+        use of the copy paths.  The dump resets the integration."""
+        torch = self.torch
+        for a in range(len(self.specs)):
+            self.rings[a][0].copy_(self.pool[a][0])
+        torch.cuda.synchronize(self.device)
+        self.batch.accumulate([r[0] for r in self.rings], stream=self.compute)
+        self.batch.dump([v[0] for v in self.vis], stream=self.compute)
+        self.compute.synchronize()
+        for a in range(len(self.specs)):
+            with torch.cuda.stream(self.d2h_stream):
+                self.host_ring[a][0][:1].copy_(self.vis[a][0][:1], non_blocking=True)
+        self.d2h_stream.synchronize()
 
     def host_block(self, a, k):
         return self.pool[a][k % self.pool_blocks]
@@ -382,18 +400,18 @@ class GpuBackend:
         self.batch.dump(outs, stream=self.compute)
         done = torch.cuda.Event()
         done.record(self.compute)
-        self.copy_stream.wait_event(done)
+        self.d2h_stream.wait_event(done)
         for a in arrays:
             slot = self.dump_count[a] & 1
             host = self.host_ring[a][slot]
             rows = {}
-            with torch.cuda.stream(self.copy_stream):
+            with torch.cuda.stream(self.d2h_stream):
                 host.copy_(outs[a], non_blocking=True)
                 for f in self.kept_channels[a]:
                     rows[f] = torch.empty(outs[a][f].shape, dtype=torch.int32, pin_memory=True)
                     rows[f].copy_(outs[a][f], non_blocking=True)
             ev = torch.cuda.Event()
-            ev.record(self.copy_stream)
+            ev.record(self.d2h_stream)
             self.d2h_done[a][slot] = ev
             self.kept.append((a, self.dump_count[a], rows))
             self.dump_count[a] += 1
