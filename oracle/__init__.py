@@ -2,8 +2,10 @@
 
 The correlation itself is the plain int64 triple loop in ``xmac_oracle.c``
 (Eq. 3 of Section 2 integrated over time as in Section 3.4.2, emitted as the
-packed lower triangle of Appendix C).  This module only builds that file with
-gcc and marshals numpy arrays to it.
+packed lower triangle of Appendix C); the same file holds the plain fp64
+statements of the fine polyphase filterbank (Section 3.2.1), the incoherent
+beam, the output remap and the packet ingest.  This module only builds that
+file with gcc and marshals numpy arrays to it.
 
 Only the test-suite, ``__graft_entry__.smoke()`` and the benchmark's CPU
 baseline may import this package.  It shares no code with the CUDA library in
@@ -34,7 +36,7 @@ def build(force: bool = False, src: str = _SRC, out: str = _LIB_PATH) -> str:
         return out
     tmp = out + f".tmp{os.getpid()}"
     cmd = ["gcc", "-O2", "-std=c11", "-fopenmp", "-fPIC", "-shared",
-           "-Wall", "-o", tmp, src]
+           "-Wall", "-o", tmp, src, "-lm"]
     subprocess.run(cmd, check=True)
     os.replace(tmp, out)
     return out
@@ -84,6 +86,10 @@ class OracleLib:
         lib.oracle_remap.restype = c_int
         lib.oracle_ingest.argtypes = [u8p, ctypes.c_int64, c_int, u8p, i64p]
         lib.oracle_ingest.restype = c_int
+        lib.oracle_fine_pfb.argtypes = [ctypes.POINTER(ctypes.c_int8), c_int, c_int, ctypes.c_int64,
+                                        ctypes.POINTER(ctypes.c_double), c_int, ctypes.c_double,
+                                        ctypes.POINTER(ctypes.c_double), u8p]
+        lib.oracle_fine_pfb.restype = c_int
         lib.oracle_set_threads.argtypes = [c_int]
         lib.oracle_set_threads.restype = c_int
         lib.oracle_threads.argtypes = []
@@ -178,6 +184,30 @@ class OracleLib:
             raise ValueError("oracle_ingest: bad arguments")
         return volt, counters
 
+    def fine_pfb(self, x: np.ndarray, window: np.ndarray, scale: float = 1.0):
+        """Fine polyphase filterbank (Section 3.2.1) of int8 coarse-channel
+        samples x [Q][N][S][2] with the window h [n_taps * 128]; returns the
+        spectra complex128 [M][Q * 128][N] and their 4+4-bit codes uint8
+        [M][Q * 128][N] (M = S / 128 - n_taps + 1, channel q * 128 + c with
+        c = (k + 64) mod 128 for DFT bin k)."""
+        xx = np.ascontiguousarray(x, dtype=np.int8)
+        h = np.ascontiguousarray(window, dtype=np.float64).ravel()
+        if xx.ndim != 4 or xx.shape[3] != 2 or h.size % 128 != 0:
+            raise ValueError("x must be int8 [Q][N][S][2] and the window n_taps * 128 long")
+        Q, N, S, _ = xx.shape
+        taps = h.size // 128
+        if S % 128 != 0 or S < 128 * taps:
+            raise ValueError("S must be a multiple of 128 and at least 128 * n_taps")
+        M = S // 128 - taps + 1
+        spec = np.zeros((M, Q * 128, N, 2), np.float64)
+        volt = np.zeros((M, Q * 128, N), np.uint8)
+        dp = ctypes.POINTER(ctypes.c_double)
+        if self.lib.oracle_fine_pfb(xx.ctypes.data_as(ctypes.POINTER(ctypes.c_int8)), Q, N, S,
+                                    h.ctypes.data_as(dp), taps, float(scale),
+                                    spec.ctypes.data_as(dp), _u8(volt)) != 0:
+            raise ValueError("oracle_fine_pfb: bad arguments")
+        return spec[..., 0] + 1j * spec[..., 1], volt
+
     def set_threads(self, n: int) -> int:
         """Set the OpenMP threads of the triangle routine; returns the count in effect."""
         return int(self.lib.oracle_set_threads(int(n)))
@@ -221,6 +251,10 @@ def remap(tri, nat_of_pfb, f_avg=1):
 
 def ingest(packets, bank):
     return default().ingest(packets, bank)
+
+
+def fine_pfb(x, window, scale=1.0):
+    return default().fine_pfb(x, window, scale)
 
 
 def pfb_order(n_inputs: int) -> np.ndarray:

@@ -39,6 +39,7 @@
  *
  * Output layout: vis[f][i(i+1)/2 + j][2] int64 (re, im), j <= i.
  */
+#include <math.h>
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
@@ -378,6 +379,98 @@ int oracle_ingest(const uint8_t *pk, int64_t n_packets, int bank, uint8_t *volt,
         }
     }
     free(seen);
+    return 0;
+}
+
+/*
+ * Fine polyphase filterbank, the second channeliser of the F stage (Section
+ * 3.2.1): a critically sampled, n_taps-tap, 128-point filter-response-weighted
+ * DFT that splits each 1.28 MHz coarse channel into 128 fine channels of
+ * 10 kHz (one output sample per 128 input samples).  The paper gives the
+ * structure (12 taps, 128 points) but not the window coefficients, so the
+ * window h[p * 128 + n] (p < n_taps, n < 128) is an input.
+ *
+ * For coarse channel q, input i and frame m:
+ *
+ *     u_m[n] = sum_{p < n_taps} h[p * 128 + n] * x_qi[(m + p) * 128 + n]     (n < 128)
+ *     Y_m[k] = sum_{n < 128} u_m[n] * exp(-2 pi i k n / 128)                 (k < 128)
+ *
+ * Readings taken here: frame m spans the input samples [128 m, 128 (m + n_taps)),
+ * and tap p weights the p-th block of 128 samples of that span (for the usual
+ * symmetric prototype filter this is the same as the convolution form); the
+ * DFT is the forward one (negative exponent); fine channel c = (k + 64) mod 128,
+ * so that c = 0 is the lowest frequency of the coarse channel and c = 64 its
+ * centre (the usual order of a channelised band).
+ *
+ * x is int8 [Q][N][S][2] (real, imaginary), S a multiple of 128 and at least
+ * 128 n_taps; M = S / 128 - n_taps + 1 frames.  Output channel q * 128 + c:
+ *   spec  double [M][Q * 128][N][2]  Y_m[k] (may be NULL);
+ *   volt  uint8  [M][Q * 128][N]     the 4+4-bit sample of Appendix A
+ *         (real part in the high nibble) of clamp(rint(scale * Y), -7, 7) per
+ *         component, rounding half to even; the X-engine's input layout, so the
+ *         two stages chain (may be NULL).
+ * Returns 0, or -1 on bad arguments.
+ */
+static int fpfb_q4(double v)
+{
+    double r = rint(v);
+    if (r > 7.0)
+        r = 7.0;
+    if (r < -7.0)
+        r = -7.0;
+    return (int)r;
+}
+
+int oracle_fine_pfb(const int8_t *x, int Q, int N, int64_t S, const double *h, int n_taps,
+                    double scale, double *spec, uint8_t *volt)
+{
+    const int L = 128;
+    if (!x || !h || Q < 1 || N < 1 || n_taps < 1 || S % L != 0 || S < (int64_t)L * n_taps)
+        return -1;
+    const int64_t M = S / L - n_taps + 1;
+    const int64_t C = (int64_t)Q * L;
+    const double two_pi = 6.283185307179586476925286766559;
+    double cs[128], sn[128];
+    for (int r = 0; r < L; ++r) {
+        cs[r] = cos(two_pi * r / L);
+        sn[r] = sin(two_pi * r / L);
+    }
+#pragma omp parallel for schedule(dynamic) collapse(2)
+    for (int q = 0; q < Q; ++q) {
+        for (int i = 0; i < N; ++i) {
+            const int8_t *xi = x + ((int64_t)q * N + i) * S * 2;
+            double ur[128], um[128];
+            for (int64_t m = 0; m < M; ++m) {
+                for (int n = 0; n < L; ++n) {
+                    double ar = 0.0, am = 0.0;
+                    for (int p = 0; p < n_taps; ++p) {
+                        const int64_t s = (m + p) * L + n;
+                        ar += h[p * L + n] * xi[2 * s];
+                        am += h[p * L + n] * xi[2 * s + 1];
+                    }
+                    ur[n] = ar;
+                    um[n] = am;
+                }
+                for (int k = 0; k < L; ++k) {
+                    double yr = 0.0, ym = 0.0;
+                    for (int n = 0; n < L; ++n) {
+                        /* exp(-2 pi i k n / L) = cos - i sin */
+                        const int r = (k * n) % L;
+                        yr += ur[n] * cs[r] + um[n] * sn[r];
+                        ym += um[n] * cs[r] - ur[n] * sn[r];
+                    }
+                    const int c = (k + L / 2) % L;
+                    const int64_t o = (m * C + (int64_t)q * L + c) * N + i;
+                    if (spec) {
+                        spec[2 * o] = yr;
+                        spec[2 * o + 1] = ym;
+                    }
+                    if (volt)
+                        volt[o] = (uint8_t)(((fpfb_q4(scale * yr) & 15) << 4) | (fpfb_q4(scale * ym) & 15));
+                }
+            }
+        }
+    }
     return 0;
 }
 

@@ -398,9 +398,116 @@ def pin_ingest_round_trip(o):
     assert len(starts) == int(d["channel_groups_per_lane"][0])
 
 
+def _pfb_x(rng, Q, N, S):
+    return rng.integers(-8, 8, (Q, N, S, 2)).astype(np.int8)
+
+
+def pin_fpfb_single_tap_is_library_fft(o):
+    """One tap of ones: every frame is the plain DFT of 128 samples, which
+    numpy's FFT computes; channel c holds bin (c + 64) mod 128."""
+    rng = _rng(41)
+    Q, N, M = 2, 3, 5
+    x = _pfb_x(rng, Q, N, 128 * M)
+    spec, _ = o.fine_pfb(x, np.ones(128), 1.0)
+    z = x[..., 0].astype(np.float64) + 1j * x[..., 1]
+    Y = np.fft.fft(z.reshape(Q, N, M, 128), axis=-1)          # [Q][N][M][k]
+    Y = np.roll(Y, 64, axis=-1)                                # index c = (k + 64) mod 128
+    want = Y.transpose(2, 0, 3, 1).reshape(M, Q * 128, N)
+    assert spec.shape == want.shape, "frame or channel count"
+    assert np.allclose(spec, want, rtol=0, atol=1e-9), "single-tap filterbank must be the forward DFT"
+
+
+def pin_fpfb_impulse_response(o):
+    """An impulse at sample s0 of one input: frame m sees it through tap
+    p = (s0 - 128 m) div 128 at point n0 = s0 mod 128, so channel c of that
+    frame is h[s0 - 128 m] exp(-2 pi i k n0 / 128) with k = (c + 64) mod 128,
+    and every other input, coarse channel and frame is zero."""
+    rng = _rng(42)
+    Q, N, taps = 2, 3, 12
+    S = 128 * (taps + 3)
+    h = rng.standard_normal(taps * 128)
+    q0, i0, s0 = 1, 2, 128 * 7 + 37
+    x = np.zeros((Q, N, S, 2), np.int8)
+    x[q0, i0, s0, 0] = 3
+    spec, _ = o.fine_pfb(x, h, 1.0)
+    M = S // 128 - taps + 1
+    want = np.zeros((M, Q * 128, N), np.complex128)
+    k = (np.arange(128) + 64) % 128
+    for m in range(M):
+        d = s0 - 128 * m
+        if 0 <= d < taps * 128:
+            want[m, q0 * 128:(q0 + 1) * 128, i0] = 3 * h[d] * np.exp(-2j * np.pi * k * (s0 % 128) / 128)
+    assert np.allclose(spec, want, rtol=0, atol=1e-9), "impulse response of the filterbank"
+
+
+def pin_fpfb_tones(o):
+    """With the window 1 / n_taps every point's taps sum to 1, so a tone at
+    bin k0 (x = A exp(2 pi i k0 s / 128), integer for k0 = 0, +-32, 64) puts
+    128 A into channel (k0 + 64) mod 128 of every frame and nothing
+    elsewhere: the sign of the exponent and the channel order."""
+    taps = 12
+    S = 128 * (taps + 2)
+    s = np.arange(S)
+    h = np.full(taps * 128, 1.0 / taps)
+    for k0, unit in ((0, np.ones(S, complex)), (32, 1j ** s), (-32, (-1j) ** s),
+                     (64, (-1.0) ** s + 0j)):
+        z = 5 * unit
+        x = np.zeros((1, 2, S, 2), np.int8)
+        x[0, 1, :, 0] = np.rint(z.real)
+        x[0, 1, :, 1] = np.rint(z.imag)
+        spec, _ = o.fine_pfb(x, h, 1.0)
+        want = np.zeros_like(spec)
+        want[:, (k0 + 64) % 128, 1] = 128 * 5
+        assert np.allclose(spec, want, rtol=0, atol=1e-9), f"tone at bin {k0}"
+
+
+def pin_fpfb_frame_shift(o):
+    """Dropping the first 128 samples drops the first frame: frames advance
+    by one block of 128 samples (critical sampling)."""
+    rng = _rng(43)
+    x = _pfb_x(rng, 1, 2, 128 * 15)
+    h = rng.standard_normal(12 * 128)
+    a, _ = o.fine_pfb(x, h, 1.0)
+    b, _ = o.fine_pfb(x[:, :, 128:], h, 1.0)
+    assert np.allclose(a[1:], b, rtol=0, atol=1e-9), "frame hop must be 128 samples"
+
+
+def pin_fpfb_quantiser(o):
+    """With one tap of ones and an impulse a + ib at the first point, every
+    channel of the frame equals a + ib exactly, so the 4+4-bit codes can be
+    checked against rounding half to even, saturation at +-7 and the nibble
+    order of Appendix A (real part high)."""
+    vals = code_values()
+    for a, b, sc, want_r, want_i in ((5, -5, 0.5, 2, -2), (7, -7, 0.5, 4, -4), (3, 1, 0.5, 2, 0),
+                                     (100, -100, 1.0, 7, -7), (9, 0, 1.0, 7, 0), (-9, 3, 1.0, -7, 3)):
+        x = np.zeros((1, 1, 128, 2), np.int8)
+        x[0, 0, 0] = (a, b)
+        spec, volt = o.fine_pfb(x, np.ones(128), sc)
+        assert np.allclose(spec, a + 1j * b), "flat spectrum of an impulse"
+        codes = volt[0, :, 0]
+        assert np.all(vals[codes >> 4] == want_r), f"real code of {a * sc}"
+        assert np.all(vals[codes & 15] == want_i), f"imaginary code of {b * sc}"
+
+
+def pin_fpfb_paper_structure(o):
+    """The printed structure: 327.68 MHz in 256 coarse subbands of 1.28 MHz,
+    12 taps x 128 points, fine channels of 10 kHz; a 12-tap filterbank over S
+    samples gives S / 128 - 11 frames of 128 channels per coarse channel."""
+    d = {k: int(v) for k, v in read_table("fine_pfb.txt")}
+    assert d["coarse_input_bandwidth_hz"] // d["coarse_subbands"] == d["coarse_channel_hz"]
+    assert d["coarse_channel_hz"] // d["fine_points"] == d["fine_channel_hz"]
+    taps, L = d["fine_taps"], d["fine_points"]
+    rng = _rng(44)
+    x = _pfb_x(rng, 2, 1, L * (taps + 4))
+    spec, volt = o.fine_pfb(x, np.ones(taps * L) / taps, 1.0)
+    assert spec.shape == volt.shape == (5, 2 * L, 1), "frames and channels of a 12-tap, 128-point bank"
+
+
 ALL_PINS = [pin_decode_table, pin_library_matmul, pin_hermitian, pin_autos,
             pin_constant_closed_form, pin_rank_one, pin_additivity, pin_permutation,
             pin_tone_phase, pin_invalid_reading, pin_paper_sizes, pin_brute_force,
             pin_beam_autos, pin_beam_brute_force, pin_pfb_order_printed,
             pin_remap_natural_order, pin_remap_paper_count, pin_ingest_golden_packet,
-            pin_ingest_rejections, pin_ingest_round_trip]
+            pin_ingest_rejections, pin_ingest_round_trip, pin_fpfb_single_tap_is_library_fft,
+            pin_fpfb_impulse_response, pin_fpfb_tones, pin_fpfb_frame_shift, pin_fpfb_quantiser,
+            pin_fpfb_paper_structure]

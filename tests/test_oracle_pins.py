@@ -100,6 +100,27 @@ MUTANTS = {
     "ingest_frame_five_bits": (
         r"const int frame = \(int\)\(w3 & 511u\);",
         "const int frame = (int)(w3 & 31u);"),
+    "fpfb_exponent_sign_flipped": (
+        r"yr \+= ur\[n\] \* cs\[r\] \+ um\[n\] \* sn\[r\];\n                        ym \+= um\[n\] \* cs\[r\] - ur\[n\] \* sn\[r\];",
+        "yr += ur[n] * cs[r] - um[n] * sn[r];\n                        ym += um[n] * cs[r] + ur[n] * sn[r];"),
+    "fpfb_channels_not_centred": (
+        r"const int c = \(k \+ L / 2\) % L;",
+        "const int c = k;"),
+    "fpfb_taps_reversed": (
+        r"ar \+= h\[p \* L \+ n\] \* xi\[2 \* s\];\n                        am \+= h\[p \* L \+ n\] \* xi\[2 \* s \+ 1\];",
+        "ar += h[(n_taps - 1 - p) * L + n] * xi[2 * s];\n                        am += h[(n_taps - 1 - p) * L + n] * xi[2 * s + 1];"),
+    "fpfb_block_time_reversed": (
+        r"const int64_t s = \(m \+ p\) \* L \+ n;",
+        "const int64_t s = (m + p) * L + (L - 1 - n);"),
+    "fpfb_round_half_away": (
+        r"double r = rint\(v\);",
+        "double r = round(v);"),
+    "fpfb_saturates_at_minus_8": (
+        r"if \(r < -7\.0\)\n        r = -7\.0;",
+        "if (r < -8.0)\n        r = -8.0;"),
+    "fpfb_nibbles_swapped": (
+        r"\(\(fpfb_q4\(scale \* yr\) & 15\) << 4\) \| \(fpfb_q4\(scale \* ym\) & 15\)",
+        "((fpfb_q4(scale * ym) & 15) << 4) | (fpfb_q4(scale * yr) & 15)"),
     "accumulate_overwrites": (
         r"vf\[2 \* p\] \+= sre;\n                vf\[2 \* p \+ 1\] \+= sim;",
         "vf[2 * p] = sre;\n                vf[2 * p + 1] = sim;"),
