@@ -399,6 +399,41 @@ int corr_ingest_packets(const uint8_t *d_packets, long long n_packets, int bank,
 int corr_remap(const int32_t *const *d_tri, int n_dumps, int n_inputs, int n_chan, int f_avg,
                const int32_t *d_nat_of_pfb, int32_t *d_out, void *stream);
 
+/*
+ * Fine polyphase filterbank, the F stage's second channeliser (Section
+ * 3.2.1): a critically sampled, n_taps-tap, 128-point filter-response-weighted
+ * DFT turning each 1.28 MHz coarse channel into 128 fine channels of 10 kHz,
+ * one output sample per 128 input samples.  For coarse channel q, input i and
+ * frame m < M = n_samples / 128 - n_taps + 1:
+ *
+ *   u_m[n] = sum_{p < n_taps} window[p * 128 + n] * x_qi[(m + p) * 128 + n]      (n < 128)
+ *   Y_m[k] = sum_{n < 128} u_m[n] * exp(-2 pi i k n / 128)                      (k < 128)
+ *
+ * written to fine channel q * 128 + c with c = (k + 64) mod 128 (c = 0 the
+ * lowest frequency of the coarse channel, c = 64 its centre).  The paper gives
+ * the 12-tap, 128-point structure but not the window, so the window is the
+ * caller's.  Arithmetic is fp32 (the window, the sums and the FFT).
+ *
+ * d_x:      device int8 [n_coarse][n_inputs][n_samples][2] (real, imaginary),
+ *           8-byte aligned; n_samples a multiple of 128 and >= 128 n_taps.
+ * d_window: device float [n_taps][128], 16-byte aligned.  n_taps: 12 (the
+ *           paper's) or 1 (a plain DFT per 128 samples); other counts give
+ *           CORR_E_UNSUPPORTED.
+ * d_volt:   device uint8 [M][n_coarse * 128][n_inputs] or NULL: the 4+4-bit
+ *           sample (Appendix A, real part in the high nibble) of
+ *           clamp(rint(scale * Y), -7, 7) per component, rounding half to even:
+ *           the X-engine's input layout, so it can be passed to corr_accumulate
+ *           with n_chan = 128 n_coarse.
+ * d_spec:   device float [M][n_coarse * 128][n_inputs][2] or NULL, 8-byte
+ *           aligned: Y itself.
+ * At least one of d_volt and d_spec must be given.  CORR_E_ARG on sizes out of
+ * range, NULL or misaligned pointers or a non-finite scale.  The caller owns
+ * every buffer; asynchronous on `stream`, allocates nothing.
+ */
+#define CORR_PFB_POINTS 128
+int corr_fine_pfb(const int8_t *d_x, int n_coarse, int n_inputs, long long n_samples, const float *d_window,
+                  int n_taps, float scale, uint8_t *d_volt, float *d_spec, void *stream);
+
 /* ------------------------------------------------------- no device allocation -- */
 
 /* Size of the library's static device scratch used by corr_xmac_noalloc. */

@@ -113,6 +113,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_incoherent_beam": ([vp, c_int, c_int, c_int, c_int, ctypes.c_uint, vp, vp], c_int),
             "corr_ingest_packets": ([vp, ctypes.c_longlong, c_int, vp, vp, vp, vp], c_int),
             "corr_remap": ([ctypes.POINTER(vp), c_int, c_int, c_int, c_int, vp, vp, vp], c_int),
+            "corr_fine_pfb": ([vp, c_int, c_int, ctypes.c_longlong, vp, c_int, ctypes.c_float, vp, vp, vp],
+                              c_int),
             "corr_batch_create": ([c_int, ctypes.POINTER(ArrayDesc)], vp),
             "corr_batch_destroy": ([vp], c_int),
             "corr_batch_workspace_bytes": ([vp], c_size),
@@ -586,6 +588,47 @@ def remap(tris, nat_of_pfb: torch.Tensor | None = None, f_avg: int = 1,
     _check(load().corr_remap(ptrs, len(tris), N, F, f_avg, perm_ptr, ctypes.c_void_p(out.data_ptr()),
                              _stream_handle(stream)), "corr_remap")
     return out
+
+
+PFB_POINTS = 128
+
+
+def fine_pfb(x: torch.Tensor, window: torch.Tensor, scale: float = 1.0, volt: bool | torch.Tensor = True,
+             spec: bool | torch.Tensor = False, stream=None):
+    """Fine polyphase filterbank (corr_fine_pfb, Section 3.2.1) of int8 coarse-
+    channel samples x [Q][N][S][2] with the window float32 [n_taps * 128]
+    (n_taps 1 or 12).  Returns (volt, spec): the 4+4-bit codes uint8
+    [M][Q * 128][N] (the X-engine's input layout) and the spectra float32
+    [M][Q * 128][N][2], M = S / 128 - n_taps + 1; pass True for a new tensor,
+    a tensor to write into, or False to skip that output (None returned)."""
+    if x.dtype != torch.int8 or x.dim() != 4 or x.shape[3] != 2 or not x.is_contiguous() or not x.is_cuda:
+        raise ValueError("x must be a contiguous int8 CUDA tensor [Q][N][S][2]")
+    if (window.dtype != torch.float32 or window.dim() != 1 or window.numel() % PFB_POINTS
+            or not window.is_contiguous() or not window.is_cuda):
+        raise ValueError("window must be a contiguous float32 CUDA tensor [n_taps * 128]")
+    Q, N, S, _ = x.shape
+    taps = window.numel() // PFB_POINTS
+    if S % PFB_POINTS or S < PFB_POINTS * taps:
+        raise ValueError("S must be a multiple of 128 and at least 128 * n_taps")
+    M = S // PFB_POINTS - taps + 1
+
+    def _out(arg, shape, dtype):
+        if arg is False or arg is None:
+            return None
+        if arg is True:
+            return torch.empty(shape, dtype=dtype, device=x.device)
+        if arg.dtype != dtype or tuple(arg.shape) != shape or not arg.is_contiguous():
+            raise ValueError(f"output must be a contiguous {dtype} {shape} tensor")
+        return arg
+    v = _out(volt, (M, Q * PFB_POINTS, N), torch.uint8)
+    sp = _out(spec, (M, Q * PFB_POINTS, N, 2), torch.float32)
+    if v is None and sp is None:
+        raise ValueError("ask for at least one of volt and spec")
+    _check(load().corr_fine_pfb(ctypes.c_void_p(x.data_ptr()), Q, N, S, ctypes.c_void_p(window.data_ptr()), taps,
+                                float(scale), ctypes.c_void_p(0 if v is None else v.data_ptr()),
+                                ctypes.c_void_p(0 if sp is None else sp.data_ptr()), _stream_handle(stream)),
+           "corr_fine_pfb")
+    return v, sp
 
 
 def unpack(volt: torch.Tensor, zero_invalid: bool = False, stream=None) -> torch.Tensor:

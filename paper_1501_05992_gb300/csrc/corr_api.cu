@@ -712,6 +712,22 @@ int corr_ingest_packets(const uint8_t *d_packets, long long n_packets, int bank,
     return ret(e == cudaSuccess ? CORR_OK : cuda_fail(e));
 }
 
+int corr_fine_pfb(const int8_t *d_x, int n_coarse, int n_inputs, long long n_samples, const float *d_window,
+                  int n_taps, float scale, uint8_t *d_volt, float *d_spec, void *stream)
+{
+    Range nvtx_range("corr_fine_pfb");
+    if (!d_x || !d_window || (!d_volt && !d_spec) || n_coarse < 1 || n_coarse > 65535 || n_inputs < 1 ||
+        n_inputs > 65536 || n_taps < 1 || n_samples % CORR_PFB_POINTS != 0 ||
+        n_samples < (long long)CORR_PFB_POINTS * n_taps || n_samples / CORR_PFB_POINTS >= (1LL << 31) ||
+        !isfinite(scale) || (reinterpret_cast<uintptr_t>(d_x) & 7) != 0 ||
+        (reinterpret_cast<uintptr_t>(d_window) & 15) != 0 || (reinterpret_cast<uintptr_t>(d_spec) & 7) != 0)
+        return ret(CORR_E_ARG);
+    if (n_taps != 1 && n_taps != 12) return ret(CORR_E_UNSUPPORTED);
+    const cudaError_t e = launch_fine_pfb(d_x, n_coarse, n_inputs, n_samples, d_window, n_taps, scale, d_volt,
+                                          d_spec, static_cast<cudaStream_t>(stream));
+    return ret(e == cudaSuccess ? CORR_OK : cuda_fail(e));
+}
+
 int corr_remap(const int32_t *const *d_tri, int n_dumps, int n_inputs, int n_chan, int f_avg,
                const int32_t *d_nat_of_pfb, int32_t *d_out, void *stream)
 {

@@ -113,6 +113,12 @@ cudaError_t launch_remap(const int32_t *const *tri, int n_dumps, int n, int n_ch
 cudaError_t launch_ingest(const uint8_t *packets, long long n_packets, int bank, uint8_t *volt, void *seen,
                           int32_t *counters, cudaStream_t s);
 
+// Fine polyphase filterbank (see corr_fine_pfb): x int8 [Q][N][S][2], window
+// float [n_taps][128] (n_taps 1 or 12), outputs volt uint8 [M][Q*128][N]
+// and/or spec float [M][Q*128][N][2] (either may be null), M = S/128 - n_taps + 1.
+cudaError_t launch_fine_pfb(const int8_t *x, int n_coarse, int n_inputs, long long n_samples, const float *window,
+                            int n_taps, float scale, uint8_t *volt, float *spec, cudaStream_t s);
+
 // Record `status` as the calling thread's last error and return it.
 int set_last_error(int status);
 

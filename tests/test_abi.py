@@ -88,3 +88,21 @@ def test_null_context_is_an_argument_error(lib_path):
     assert lib.corr_unpack(None, 4, 0, 4, None, 0, None) == corr.CORR_E_ARG
     assert lib.corr_unpack(None, 4, 2, 4, None, 0, None) == corr.CORR_E_ARG
     assert lib.corr_unpack(None, 0, 2, 4, None, 0, None) == corr.CORR_OK
+
+
+def test_fine_pfb_rejects_bad_arguments_without_touching_a_device(lib_path):
+    lib = corr.load()
+    fake = ctypes.c_void_p(1 << 20)           # aligned, never dereferenced: every call below fails its checks
+    null = ctypes.c_void_p(0)
+    cases = [
+        ((null, 1, 8, 1536, fake, 12, 1.0, fake, null, null), corr.CORR_E_ARG),        # no input
+        ((fake, 1, 8, 1536, fake, 12, 1.0, null, null, null), corr.CORR_E_ARG),        # no output
+        ((fake, 1, 8, 1500, fake, 12, 1.0, fake, null, null), corr.CORR_E_ARG),        # not whole blocks
+        ((fake, 1, 8, 1408, fake, 12, 1.0, fake, null, null), corr.CORR_E_ARG),        # fewer than 12 blocks
+        ((fake, 0, 8, 1536, fake, 12, 1.0, fake, null, null), corr.CORR_E_ARG),
+        ((fake, 1, 8, 1536, ctypes.c_void_p((1 << 20) + 4), 12, 1.0, fake, null, null), corr.CORR_E_ARG),
+        ((fake, 1, 8, 1536, fake, 12, float("nan"), fake, null, null), corr.CORR_E_ARG),
+        ((fake, 1, 8, 1536, fake, 5, 1.0, fake, null, null), corr.CORR_E_UNSUPPORTED),
+    ]
+    for args, want in cases:
+        assert lib.corr_fine_pfb(*args) == want, args
