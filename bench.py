@@ -379,7 +379,52 @@ def measure_extras(arrays, volts, outs, stream_, dev, peaks, src):
         res["remap_2x2"] = {"ms": ms, "bytes": nbytes, "gbs": nbytes / ms / 1e6,
                             "frac": (nbytes / ms / 1e6) / hbm if hbm else None,
                             "peak_gbs": hbm, "bound": "hbm"}
+    if n % 8 == 0 and f % 128 == 0:
+        res["fine_pfb"] = measure_fine_pfb(n, f // 128, t, stream_, dev)
     return res
+
+
+FP32_LANES_PER_SM = 128          # fp32 FMA lanes per SM (4 sub-partitions x 32)
+
+
+def measure_fine_pfb(n, n_coarse, frames, stream_, dev):
+    """The F stage's fine filterbank (12 taps, 128 points) producing one
+    integration's voltages for every coarse channel: n_coarse x n inputs x
+    `frames` output samples from seeded int8 coarse-channel noise, the codes
+    written in the X-engine's input layout.  The kernel is bound by fp32
+    arithmetic: 12 x 128 complex-by-real multiply-adds (4 flops each) and a
+    128-point FFT (5 N log2 N = 4480 flops) per frame and input, against the
+    fp32 peak of 128 FMA lanes x 2 flops per SM and clock at the maximum SM
+    clock (2070 MHz)."""
+    import numpy as np
+    import torch
+    from paper_1501_05992_gb300 import corr
+    from synth import coarse
+    taps = 12
+    S = 128 * (frames + taps - 1)
+    g = torch.Generator(device=dev)
+    g.manual_seed(1505)
+    x = torch.empty((n_coarse, n, S, 2), dtype=torch.int8, device=dev)
+    for q in range(n_coarse):       # N(0, 8^2) per component, rounded and clipped
+        x[q] = torch.randn((n, S, 2), device=dev, generator=g).mul_(8.0).round_().clamp_(-127, 127).to(torch.int8)
+    h_np = coarse.kaiser_sinc_window(taps)
+    h = torch.from_numpy(h_np.astype(np.float32)).to(dev)
+    scale = coarse.output_scale(h_np, 8.0)
+    volt = torch.empty((frames, n_coarse * 128, n), dtype=torch.uint8, device=dev)
+    torch.cuda.synchronize(dev)
+    ms = _time_ms(lambda: corr.fine_pfb(x, h, scale, volt=volt, stream=stream_), stream_)
+    units = n_coarse * n * frames
+    flops = units * (taps * 128 * 4 + 5 * 128 * 7)
+    sm = torch.cuda.get_device_properties(dev).multi_processor_count
+    peak = sm * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    tflops = flops / ms / 1e9
+    out = {"ms": ms, "frames": frames, "coarse_channels": n_coarse, "inputs": n,
+           "x_real_time": frames / SAMPLE_RATE_HZ / (ms * 1e-3), "tflops": tflops, "peak_tflops": peak,
+           "frac": tflops / peak, "bound": "alu",
+           "peak_note": f"{sm} SMs x {FP32_LANES_PER_SM} fp32 lanes x 2 flops x 2.07 GHz",
+           "bytes": x.numel() + volt.numel()}
+    del x, volt
+    return out
 
 
 def run_ours(args, world, rank, local):

@@ -17,12 +17,16 @@
 // Work decomposition.  A CTA of 8 warps takes 8 consecutive inputs of one
 // coarse channel over a run of frames; warp w owns input 8 blockIdx.x + w and
 // lane l the points n = 4 l .. 4 l + 3 (one 8-byte load per lane covers a
-// 128-sample block, coalesced).  Frames go in groups of G = 8: the G + n_taps - 1
+// 128-sample block, coalesced).  Frames go in groups of G = 4: the G + n_taps - 1
 // blocks that feed a group are loaded once each (from L1 for the n_taps - 1
 // shared with the previous group), converted to float once, and each block is
 // multiply-added into the accumulators of the frames it reaches (all register
 // indices are compile-time, the block loop being unrolled).  The window sits
-// in registers (4 n_taps per lane), the accumulators too (8 G per lane).
+// in registers (4 n_taps per lane), the accumulators too (8 G per lane), which
+// keeps a thread at 128 registers: two CTAs (16 warps) per SM.  The lane's
+// points are handled in pairs (j, j + 1) with the paired fp32 instructions of
+// sm_100+ (fma/mul/add over a float2), which halves the instruction count of
+// the windowing and of the butterflies.
 // The 128-point DFT of a frame is then done in the warp with n = 4 n1 + n2
 // (n1 = lane, n2 = register j):
 //
@@ -44,7 +48,7 @@ namespace {
 constexpr int kPfbPoints = 128;
 constexpr int kPfbWarps = 8;                  // inputs per CTA
 constexpr int kPfbThreads = kPfbWarps * 32;
-constexpr int kPfbFramesPerCta = 120;         // frames per CTA (whole groups of 8)
+constexpr int kPfbFramesPerCta = 120;         // frames per CTA (whole groups of 4)
 
 struct PfbArgs {
     const int8_t *x;      // [Q][N][S][2]
@@ -81,8 +85,14 @@ __device__ __forceinline__ float2 w128(int r)
     return make_float2(c, s);
 }
 
+// Paired fp32 arithmetic (sm_100+): one instruction does the two lanes of a float2.
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 dup2(float v) { return make_float2(v, v); }
+
 template <int TAPS, int G>
-__global__ void __launch_bounds__(kPfbThreads, 1) fpfb_kernel(PfbArgs a)
+__global__ void __launch_bounds__(kPfbThreads, 2) fpfb_kernel(PfbArgs a)
 {
     // G frames per group (kPfbFramesPerCta is a multiple of G); B blocks feed them
     static_assert(kPfbFramesPerCta % G == 0, "whole groups per CTA");
@@ -98,55 +108,73 @@ __global__ void __launch_bounds__(kPfbThreads, 1) fpfb_kernel(PfbArgs a)
     const long long n_blocks = a.S / kPfbPoints;
     const size_t C = size_t(a.Q) * kPfbPoints;
 
-    // the window at this lane's points, for every tap
-    float hr[TAPS][4];
+    // Each lane's four points j = 0..3 are handled as two pairs (j, j + 1), so
+    // that every multiply-add of the windowing and of the transforms is a
+    // paired instruction over two points (or two transforms).
+    // The window at this lane's points, for every tap: h2[p][0] = (h[4l], h[4l+1]), ...
+    float2 h2[TAPS][2];
 #pragma unroll
     for (int p = 0; p < TAPS; ++p) {
         const float4 v = *reinterpret_cast<const float4 *>(a.h + p * kPfbPoints + 4 * lane);
-        hr[p][0] = v.x;
-        hr[p][1] = v.y;
-        hr[p][2] = v.z;
-        hr[p][3] = v.w;
+        h2[p][0] = make_float2(v.x, v.y);
+        h2[p][1] = make_float2(v.z, v.w);
     }
     // twiddles: DIF stage with half span d uses W_{2d}^{l mod d} = W128^{(l mod d) 64 / d}
-    // on the upper lane of each pair; after the transform lane l holds k1 = bitrev5(l)
-    float2 tw[5];
-    float sg[5];
+    // on the upper lane of each pair (1 on the lower); after the transform lane l
+    // holds k1 = bitrev5(l).  Kept as duplicated pairs for the paired arithmetic.
+    float2 sg2[5], wr2[5], wi2[5], nwi2[5];
 #pragma unroll
     for (int st = 0; st < 5; ++st) {
         const int d = 16 >> st;
         const bool upper = (lane & d) != 0;
-        tw[st] = upper ? w128((lane & (d - 1)) * (64 / d)) : make_float2(1.0f, 0.0f);
-        sg[st] = upper ? -1.0f : 1.0f;
+        const float2 w = upper ? w128((lane & (d - 1)) * (64 / d)) : make_float2(1.0f, 0.0f);
+        sg2[st] = dup2(upper ? -1.0f : 1.0f);
+        wr2[st] = dup2(w.x);
+        wi2[st] = dup2(w.y);
+        nwi2[st] = dup2(-w.y);
     }
     const int k1 = __brev(unsigned(lane)) >> 27;
+    // W128^{j k1} for j = 0..3, as pairs (j = 0, 1) and (j = 2, 3)
     const float2 t1 = w128(k1), t2 = w128(2 * k1), t3 = w128(3 * k1);
+    const float2 tr01 = make_float2(1.0f, t1.x), ti01 = make_float2(0.0f, t1.y), nti01 = make_float2(0.0f, -t1.y);
+    const float2 tr23 = make_float2(t2.x, t3.x), ti23 = make_float2(t2.y, t3.y), nti23 = make_float2(-t2.y, -t3.y);
+    const float2 bias = dup2(-8388736.0f), minus1 = dup2(-1.0f), scale2 = dup2(a.scale);
 
     const int8_t *xi = a.x + (size_t(q) * a.N + (active ? i : 0)) * size_t(a.S) * 2;
 
     for (int g0 = m0; g0 < m1; g0 += G) {
-        float ar[G][4], am[G][4];
+        // ar[f][h] = real parts of frame g0 + f at points (2h, 2h + 1) of this lane; am imaginary
+        float2 ar[G][2], am[G][2];
 #pragma unroll
         for (int f = 0; f < G; ++f)
 #pragma unroll
-            for (int j = 0; j < 4; ++j) ar[f][j] = am[f][j] = 0.0f;
+            for (int hh = 0; hh < 2; ++hh) ar[f][hh] = am[f][hh] = make_float2(0.0f, 0.0f);
 #pragma unroll
         for (int bb = 0; bb < B; ++bb) {
             const long long b = g0 + bb;
             uint2 w = make_uint2(0u, 0u);
             if (active && b < n_blocks)
                 w = *reinterpret_cast<const uint2 *>(xi + (b * kPfbPoints + 4 * lane) * 2);
-            float xr[4], xm[4];
-            bytes_to_float(w.x, xr[0], xm[0], xr[1], xm[1]);
-            bytes_to_float(w.y, xr[2], xm[2], xr[3], xm[3]);
+            // bytes (re0, im0, re1, im1 | re2, im2, re3, im3) -> floats; the signed
+            // byte s becomes 2^23 + s + 128 in the float's mantissa, then the bias goes
+            const uint32_t u0 = w.x ^ 0x80808080u, u1 = w.y ^ 0x80808080u;
+            float2 xr[2], xm[2];
+            xr[0] = add2(make_float2(__int_as_float(int(__byte_perm(u0, 0x4B000000u, 0x7440))),
+                                     __int_as_float(int(__byte_perm(u0, 0x4B000000u, 0x7442)))), bias);
+            xm[0] = add2(make_float2(__int_as_float(int(__byte_perm(u0, 0x4B000000u, 0x7441))),
+                                     __int_as_float(int(__byte_perm(u0, 0x4B000000u, 0x7443)))), bias);
+            xr[1] = add2(make_float2(__int_as_float(int(__byte_perm(u1, 0x4B000000u, 0x7440))),
+                                     __int_as_float(int(__byte_perm(u1, 0x4B000000u, 0x7442)))), bias);
+            xm[1] = add2(make_float2(__int_as_float(int(__byte_perm(u1, 0x4B000000u, 0x7441))),
+                                     __int_as_float(int(__byte_perm(u1, 0x4B000000u, 0x7443)))), bias);
 #pragma unroll
             for (int p = 0; p < TAPS; ++p) {
                 const int f = bb - p;                  // frame g0 + f takes this block as tap p
                 if (f >= 0 && f < G) {
 #pragma unroll
-                    for (int j = 0; j < 4; ++j) {
-                        ar[f][j] = fmaf(hr[p][j], xr[j], ar[f][j]);
-                        am[f][j] = fmaf(hr[p][j], xm[j], am[f][j]);
+                    for (int hh = 0; hh < 2; ++hh) {
+                        ar[f][hh] = fma2(h2[p][hh], xr[hh], ar[f][hh]);
+                        am[f][hh] = fma2(h2[p][hh], xm[hh], am[f][hh]);
                     }
                 }
             }
@@ -155,48 +183,45 @@ __global__ void __launch_bounds__(kPfbThreads, 1) fpfb_kernel(PfbArgs a)
         for (int f = 0; f < G; ++f) {
             const int m = g0 + f;
             if (m >= m1) break;                        // uniform across the CTA
-            float zr[4], zm[4];
-#pragma unroll
-            for (int j = 0; j < 4; ++j) {
-                zr[j] = ar[f][j];
-                zm[j] = am[f][j];
-            }
+            // zr[hh] = real parts of transforms (2hh, 2hh + 1), zm imaginary
+            float2 zr[2] = {ar[f][0], ar[f][1]}, zm[2] = {am[f][0], am[f][1]};
             // 32-point DIF across lanes, four transforms at once
 #pragma unroll
             for (int st = 0; st < 5; ++st) {
                 const int d = 16 >> st;
 #pragma unroll
-                for (int j = 0; j < 4; ++j) {
-                    const float vr = __shfl_xor_sync(0xffffffffu, zr[j], d);
-                    const float vm = __shfl_xor_sync(0xffffffffu, zm[j], d);
+                for (int hh = 0; hh < 2; ++hh) {
+                    const float2 vr = make_float2(__shfl_xor_sync(0xffffffffu, zr[hh].x, d),
+                                                  __shfl_xor_sync(0xffffffffu, zr[hh].y, d));
+                    const float2 vm = make_float2(__shfl_xor_sync(0xffffffffu, zm[hh].x, d),
+                                                  __shfl_xor_sync(0xffffffffu, zm[hh].y, d));
                     // lower lane: own + partner; upper lane: (partner - own) * twiddle
-                    const float sr = fmaf(sg[st], zr[j], vr), sm = fmaf(sg[st], zm[j], vm);
-                    zr[j] = sr * tw[st].x - sm * tw[st].y;
-                    zm[j] = sr * tw[st].y + sm * tw[st].x;
+                    const float2 sr = fma2(sg2[st], zr[hh], vr), sm = fma2(sg2[st], zm[hh], vm);
+                    zr[hh] = fma2(sm, nwi2[st], mul2(sr, wr2[st]));
+                    zm[hh] = fma2(sm, wr2[st], mul2(sr, wi2[st]));
                 }
             }
-            // twiddle W128^{j k1}, then the 4-point DFT over j (W4 = -i)
+            // twiddle W128^{j k1}
             {
-                float r, s;
-                r = zr[1] * t1.x - zm[1] * t1.y; s = zr[1] * t1.y + zm[1] * t1.x; zr[1] = r; zm[1] = s;
-                r = zr[2] * t2.x - zm[2] * t2.y; s = zr[2] * t2.y + zm[2] * t2.x; zr[2] = r; zm[2] = s;
-                r = zr[3] * t3.x - zm[3] * t3.y; s = zr[3] * t3.y + zm[3] * t3.x; zr[3] = r; zm[3] = s;
+                const float2 r0 = fma2(zm[0], nti01, mul2(zr[0], tr01)), s0 = fma2(zm[0], tr01, mul2(zr[0], ti01));
+                const float2 r1 = fma2(zm[1], nti23, mul2(zr[1], tr23)), s1 = fma2(zm[1], tr23, mul2(zr[1], ti23));
+                zr[0] = r0; zm[0] = s0; zr[1] = r1; zm[1] = s1;
             }
-            const float e0r = zr[0] + zr[2], e0m = zm[0] + zm[2];
-            const float e1r = zr[0] - zr[2], e1m = zm[0] - zm[2];
-            const float o0r = zr[1] + zr[3], o0m = zm[1] + zm[3];
-            const float o1r = zr[1] - zr[3], o1m = zm[1] - zm[3];
-            float yr[4], ym[4];
-            yr[0] = e0r + o0r; ym[0] = e0m + o0m;
-            yr[2] = e0r - o0r; ym[2] = e0m - o0m;
-            yr[1] = e1r + o1m; ym[1] = e1m - o1r;      // e1 - i o1
-            yr[3] = e1r - o1m; ym[3] = e1m + o1r;      // e1 + i o1
+            // 4-point DFT over j (W4 = -i): (e0, o0) = (Z0 + Z2, Z1 + Z3), (e1, o1) = (Z0 - Z2, Z1 - Z3)
+            const float2 eor = add2(zr[0], zr[1]), eom = add2(zm[0], zm[1]);
+            const float2 e1r_o1r = fma2(zr[1], minus1, zr[0]), e1m_o1m = fma2(zm[1], minus1, zm[0]);
+            float2 y[4];
+            y[0] = make_float2(eor.x + eor.y, eom.x + eom.y);
+            y[2] = make_float2(eor.x - eor.y, eom.x - eom.y);
+            y[1] = make_float2(e1r_o1r.x + e1m_o1m.y, e1m_o1m.x - e1r_o1r.y);     // e1 - i o1
+            y[3] = make_float2(e1r_o1r.x - e1m_o1m.y, e1m_o1m.x + e1r_o1r.y);     // e1 + i o1
 #pragma unroll
             for (int k2 = 0; k2 < 4; ++k2) {
                 const int c = k1 + 32 * ((k2 + 2) & 3);   // (k1 + 32 k2 + 64) mod 128
                 if (a.spec && active)
-                    a.spec[(size_t(m) * C + size_t(q) * kPfbPoints + c) * a.N + i] = make_float2(yr[k2], ym[k2]);
-                const int cr = quant4(yr[k2] * a.scale), cm = quant4(ym[k2] * a.scale);
+                    a.spec[(size_t(m) * C + size_t(q) * kPfbPoints + c) * a.N + i] = y[k2];
+                const float2 v = mul2(y[k2], scale2);
+                const int cr = quant4(v.x), cm = quant4(v.y);
                 tile[f][c][warp] = uint8_t(((cr & 15) << 4) | (cm & 15));
             }
         }
@@ -236,9 +261,9 @@ cudaError_t launch_fine_pfb(const int8_t *x, int n_coarse, int n_inputs, long lo
     a.scale = scale;
     const dim3 grid((n_inputs + kPfbWarps - 1) / kPfbWarps, (a.M + kPfbFramesPerCta - 1) / kPfbFramesPerCta, n_coarse);
     if (n_taps == 12)
-        fpfb_kernel<12, 8><<<grid, kPfbThreads, 0, s>>>(a);
+        fpfb_kernel<12, 4><<<grid, kPfbThreads, 0, s>>>(a);
     else
-        fpfb_kernel<1, 8><<<grid, kPfbThreads, 0, s>>>(a);
+        fpfb_kernel<1, 4><<<grid, kPfbThreads, 0, s>>>(a);
     return cudaGetLastError();
 }
 
