@@ -135,3 +135,42 @@ def test_mode_outputs_stay_inside_their_buffers():
     torch.cuda.synchronize()
     assert _guards_intact(bb, torch.int32) and _guards_intact(br, torch.int32)
     assert np.array_equal(ob.cpu().numpy(), oracle.beam(volt.cpu().numpy(), 4))
+
+
+def test_fine_pfb_full_band_sampled():
+    """The fine filterbank at the benchmark's size (24 coarse channels x 256
+    inputs x 5000 frames, 12 taps, codes only, as timed), checked on sampled
+    (coarse channel, input) streams over a run of frames each: the codes
+    equal the oracle's except within the fp32 bound of a rounding boundary."""
+    from synth import coarse
+    Q, N, M, taps = 24, 256, 5000, 12
+    S = 128 * (M + taps - 1)
+    g = torch.Generator(device="cuda")
+    g.manual_seed(1505)
+    x = torch.empty((Q, N, S, 2), dtype=torch.int8, device="cuda")
+    for q in range(Q):
+        x[q] = torch.randn((N, S, 2), device="cuda", generator=g).mul_(8.0).round_().clamp_(-127, 127).to(torch.int8)
+    h = coarse.kaiser_sinc_window(taps).astype(np.float32)
+    scale = coarse.output_scale(h.astype(np.float64), 8.0)
+    codes, _ = corr.fine_pfb(x, torch.from_numpy(h).cuda(), scale)
+    torch.cuda.synchronize()
+    vals = np.array([v if v < 8 else v - 16 for v in range(16)])
+    rng = np.random.default_rng(5)
+    checked = 0
+    for q, i, m0 in [(0, 0, 0), (23, 255, M - 40), (11, 128, 2500)] + \
+            [(int(a), int(b), int(c)) for a, b, c in zip(rng.integers(0, Q, 5), rng.integers(0, N, 5),
+                                                         rng.integers(0, M - 40, 5))]:
+        xs = x[q, i, m0 * 128:(m0 + 40 + taps - 1) * 128].cpu().numpy()[None, None]
+        spec, want = oracle.fine_pfb(xs, h.astype(np.float64), scale)      # frames m0 .. m0 + 39
+        got = codes[m0:m0 + 40, q * 128:(q + 1) * 128, i].cpu().numpy()
+        want = want[:, :, 0]
+        spec = spec[:, :, 0] * scale
+        a = (np.abs(xs[0, 0, :, 0].astype(np.float64)) + np.abs(xs[0, 0, :, 1])).reshape(-1, 128)
+        ah = np.abs(h.astype(np.float64)).reshape(taps, 128)
+        bound = np.array([sum(a[m + p] @ ah[p] for p in range(taps)) for m in range(40)]) * 64 * 2.0 ** -24 * scale
+        for part, shift, exact in (("real", 4, spec.real), ("imag", 0, spec.imag)):
+            gv, wv = vals[(got >> shift) & 15], vals[(want >> shift) & 15]
+            near = np.abs(np.abs(exact - np.floor(exact)) - 0.5) <= bound[:, None]
+            assert ((gv == wv) | near).all(), (part, q, i, m0)
+        checked += got.size
+    assert checked == 8 * 40 * 128
