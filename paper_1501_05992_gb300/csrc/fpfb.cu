@@ -33,9 +33,10 @@
 //     Y[k1 + 32 k2] = sum_{n2 < 4} W4^{n2 k2} W128^{n2 k1} sum_{n1 < 32} x[4 n1 + n2] W32^{n1 k1}
 //
 // i.e. four 32-point DIF transforms across lanes (shuffles; lane l ends with
-// k1 = bitrev5(l)), a twiddle, and a 4-point DFT inside each lane.  The codes
-// of a group go through shared memory so that each output row carries the 8
-// inputs of the CTA together.
+// k1 = bitrev5(l)), a twiddle, and a 4-point DFT inside each lane; two frames
+// go through the transform together so that their shuffles and arithmetic
+// interleave.  The codes of a group go through shared memory so that each
+// output row carries the 8 inputs of the CTA together.
 //
 // The work is fp32 arithmetic (about 10.6 kflop per frame and input: 12 x 128
 // complex-by-real multiply-adds and a 128-point FFT) against 256 bytes read and
@@ -69,12 +70,6 @@ __device__ __forceinline__ void bytes_to_float(uint32_t w, float &b0, float &b1,
     b1 = __int_as_float(int(__byte_perm(u, 0x4B000000u, 0x7441))) - 8388736.0f;
     b2 = __int_as_float(int(__byte_perm(u, 0x4B000000u, 0x7442))) - 8388736.0f;
     b3 = __int_as_float(int(__byte_perm(u, 0x4B000000u, 0x7443))) - 8388736.0f;
-}
-
-__device__ __forceinline__ int quant4(float v)
-{
-    const int r = __float2int_rn(v);                  // round half to even
-    return r > 7 ? 7 : (r < -7 ? -7 : r);
 }
 
 // exp(-2 pi i r / 128)
@@ -138,7 +133,7 @@ __global__ void __launch_bounds__(kPfbThreads, 2) fpfb_kernel(PfbArgs a)
     const float2 t1 = w128(k1), t2 = w128(2 * k1), t3 = w128(3 * k1);
     const float2 tr01 = make_float2(1.0f, t1.x), ti01 = make_float2(0.0f, t1.y), nti01 = make_float2(0.0f, -t1.y);
     const float2 tr23 = make_float2(t2.x, t3.x), ti23 = make_float2(t2.y, t3.y), nti23 = make_float2(-t2.y, -t3.y);
-    const float2 bias = dup2(-8388736.0f), minus1 = dup2(-1.0f), scale2 = dup2(a.scale);
+    const float2 bias = dup2(-8388736.0f), minus1 = dup2(-1.0f), scale2 = dup2(a.scale), magic2 = dup2(12582912.0f);
 
     const int8_t *xi = a.x + (size_t(q) * a.N + (active ? i : 0)) * size_t(a.S) * 2;
 
@@ -180,49 +175,64 @@ __global__ void __launch_bounds__(kPfbThreads, 2) fpfb_kernel(PfbArgs a)
             }
         }
 #pragma unroll
-        for (int f = 0; f < G; ++f) {
-            const int m = g0 + f;
-            if (m >= m1) break;                        // uniform across the CTA
-            // zr[hh] = real parts of transforms (2hh, 2hh + 1), zm imaginary
-            float2 zr[2] = {ar[f][0], ar[f][1]}, zm[2] = {am[f][0], am[f][1]};
-            // 32-point DIF across lanes, four transforms at once
+        for (int f0 = 0; f0 < G; f0 += 2) {
+            if (g0 + f0 >= m1) break;                  // uniform across the CTA
+            float2 zr[2][2], zm[2][2];
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                zr[u][0] = ar[f0 + u][0]; zr[u][1] = ar[f0 + u][1];
+                zm[u][0] = am[f0 + u][0]; zm[u][1] = am[f0 + u][1];
+            }
 #pragma unroll
             for (int st = 0; st < 5; ++st) {
                 const int d = 16 >> st;
+                float2 vr[2][2], vm[2][2];
 #pragma unroll
-                for (int hh = 0; hh < 2; ++hh) {
-                    const float2 vr = make_float2(__shfl_xor_sync(0xffffffffu, zr[hh].x, d),
-                                                  __shfl_xor_sync(0xffffffffu, zr[hh].y, d));
-                    const float2 vm = make_float2(__shfl_xor_sync(0xffffffffu, zm[hh].x, d),
-                                                  __shfl_xor_sync(0xffffffffu, zm[hh].y, d));
-                    // lower lane: own + partner; upper lane: (partner - own) * twiddle
-                    const float2 sr = fma2(sg2[st], zr[hh], vr), sm = fma2(sg2[st], zm[hh], vm);
-                    zr[hh] = fma2(sm, nwi2[st], mul2(sr, wr2[st]));
-                    zm[hh] = fma2(sm, wr2[st], mul2(sr, wi2[st]));
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        vr[u][hh] = make_float2(__shfl_xor_sync(0xffffffffu, zr[u][hh].x, d),
+                                                __shfl_xor_sync(0xffffffffu, zr[u][hh].y, d));
+                        vm[u][hh] = make_float2(__shfl_xor_sync(0xffffffffu, zm[u][hh].x, d),
+                                                __shfl_xor_sync(0xffffffffu, zm[u][hh].y, d));
+                    }
+#pragma unroll
+                for (int u = 0; u < 2; ++u)
+#pragma unroll
+                    for (int hh = 0; hh < 2; ++hh) {
+                        const float2 sr = fma2(sg2[st], zr[u][hh], vr[u][hh]), sm = fma2(sg2[st], zm[u][hh], vm[u][hh]);
+                        zr[u][hh] = fma2(sm, nwi2[st], mul2(sr, wr2[st]));
+                        zm[u][hh] = fma2(sm, wr2[st], mul2(sr, wi2[st]));
+                    }
+            }
+#pragma unroll
+            for (int u = 0; u < 2; ++u) {
+                const int f = f0 + u, m = g0 + f;
+                {
+                    const float2 r0 = fma2(zm[u][0], nti01, mul2(zr[u][0], tr01)), s0 = fma2(zm[u][0], tr01, mul2(zr[u][0], ti01));
+                    const float2 r1 = fma2(zm[u][1], nti23, mul2(zr[u][1], tr23)), s1 = fma2(zm[u][1], tr23, mul2(zr[u][1], ti23));
+                    zr[u][0] = r0; zm[u][0] = s0; zr[u][1] = r1; zm[u][1] = s1;
                 }
-            }
-            // twiddle W128^{j k1}
-            {
-                const float2 r0 = fma2(zm[0], nti01, mul2(zr[0], tr01)), s0 = fma2(zm[0], tr01, mul2(zr[0], ti01));
-                const float2 r1 = fma2(zm[1], nti23, mul2(zr[1], tr23)), s1 = fma2(zm[1], tr23, mul2(zr[1], ti23));
-                zr[0] = r0; zm[0] = s0; zr[1] = r1; zm[1] = s1;
-            }
-            // 4-point DFT over j (W4 = -i): (e0, o0) = (Z0 + Z2, Z1 + Z3), (e1, o1) = (Z0 - Z2, Z1 - Z3)
-            const float2 eor = add2(zr[0], zr[1]), eom = add2(zm[0], zm[1]);
-            const float2 e1r_o1r = fma2(zr[1], minus1, zr[0]), e1m_o1m = fma2(zm[1], minus1, zm[0]);
-            float2 y[4];
-            y[0] = make_float2(eor.x + eor.y, eom.x + eom.y);
-            y[2] = make_float2(eor.x - eor.y, eom.x - eom.y);
-            y[1] = make_float2(e1r_o1r.x + e1m_o1m.y, e1m_o1m.x - e1r_o1r.y);     // e1 - i o1
-            y[3] = make_float2(e1r_o1r.x - e1m_o1m.y, e1m_o1m.x + e1r_o1r.y);     // e1 + i o1
+                const float2 eor = add2(zr[u][0], zr[u][1]), eom = add2(zm[u][0], zm[u][1]);
+                const float2 e1r_o1r = fma2(zr[u][1], minus1, zr[u][0]), e1m_o1m = fma2(zm[u][1], minus1, zm[u][0]);
+                float2 y[4];
+                y[0] = make_float2(eor.x + eor.y, eom.x + eom.y);
+                y[2] = make_float2(eor.x - eor.y, eom.x - eom.y);
+                y[1] = make_float2(e1r_o1r.x + e1m_o1m.y, e1m_o1m.x - e1r_o1r.y);
+                y[3] = make_float2(e1r_o1r.x - e1m_o1m.y, e1m_o1m.x + e1r_o1r.y);
 #pragma unroll
-            for (int k2 = 0; k2 < 4; ++k2) {
-                const int c = k1 + 32 * ((k2 + 2) & 3);   // (k1 + 32 k2 + 64) mod 128
-                if (a.spec && active)
-                    a.spec[(size_t(m) * C + size_t(q) * kPfbPoints + c) * a.N + i] = y[k2];
-                const float2 v = mul2(y[k2], scale2);
-                const int cr = quant4(v.x), cm = quant4(v.y);
-                tile[f][c][warp] = uint8_t(((cr & 15) << 4) | (cm & 15));
+                for (int k2 = 0; k2 < 4; ++k2) {
+                    const int c = k1 + 32 * ((k2 + 2) & 3);
+                    if (a.spec && active && m < m1)
+                        a.spec[(size_t(m) * C + size_t(q) * kPfbPoints + c) * a.N + i] = y[k2];
+                    // clamp to [-7, 7], then adding 1.5 * 2^23 rounds to the nearest
+                    // integer, ties to even, and leaves it (two's complement) in the
+                    // low mantissa bits
+                    const float2 v = mul2(y[k2], scale2);
+                    const float2 w = add2(make_float2(fminf(fmaxf(v.x, -7.0f), 7.0f), fminf(fmaxf(v.y, -7.0f), 7.0f)),
+                                          magic2);
+                    tile[f][c][warp] = uint8_t(((__float_as_uint(w.x) & 15u) << 4) | (__float_as_uint(w.y) & 15u));
+                }
             }
         }
         if (a.volt) {
