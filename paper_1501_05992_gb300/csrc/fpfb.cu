@@ -61,17 +61,6 @@ struct PfbArgs {
     float scale;
 };
 
-// signed bytes of w as floats: (s + 128) placed in the mantissa of 2^23, then
-// 2^23 + 128 subtracted (exact for every byte)
-__device__ __forceinline__ void bytes_to_float(uint32_t w, float &b0, float &b1, float &b2, float &b3)
-{
-    const uint32_t u = w ^ 0x80808080u;
-    b0 = __int_as_float(int(__byte_perm(u, 0x4B000000u, 0x7440))) - 8388736.0f;
-    b1 = __int_as_float(int(__byte_perm(u, 0x4B000000u, 0x7441))) - 8388736.0f;
-    b2 = __int_as_float(int(__byte_perm(u, 0x4B000000u, 0x7442))) - 8388736.0f;
-    b3 = __int_as_float(int(__byte_perm(u, 0x4B000000u, 0x7443))) - 8388736.0f;
-}
-
 // exp(-2 pi i r / 128)
 __device__ __forceinline__ float2 w128(int r)
 {
