@@ -53,7 +53,7 @@ WORKLOADS = {
 def parse_args():
     ap = argparse.ArgumentParser(description=__doc__)
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=16)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--path", default="auto", choices=["auto", "cudacore", "mma_i8", "tc_fp8"])
@@ -73,44 +73,65 @@ def parse_args():
 
 # ---------------------------------------------------------------- clocks ---
 class ClockSampler:
-    """nvidia-smi clock / throttle sampling while the timed region runs."""
+    """nvidia-smi clock / throttle sampling around the timed region: started
+    before the warm-up (nvidia-smi takes a while to produce its first line),
+    one reading every 50 ms, and only the readings that arrive between
+    mark_start() and mark_stop() (plus one interval) are reported."""
 
     FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+    INTERVAL_MS = 50
 
     def __init__(self, device_index: int):
         self.idx = device_index
         self.proc = None
-        self.lines: list[str] = []
+        self.lines: list[tuple[float, str]] = []
+        self.t_start = self.t_stop = None
 
     def start(self):
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", str(self.INTERVAL_MS)],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self._t = threading.Thread(target=self._read, daemon=True)
             self._t.start()
         except (FileNotFoundError, OSError):
             self.proc = None
+            return
+        t0 = time.perf_counter()
+        while not self.lines and time.perf_counter() - t0 < 3.0 and self.proc.poll() is None:
+            time.sleep(0.01)
 
     def _read(self):
         for line in self.proc.stdout:
-            self.lines.append(line.strip())
+            self.lines.append((time.perf_counter(), line.strip()))
+
+    def mark_start(self):
+        self.t_start = time.perf_counter()
+
+    def mark_stop(self):
+        self.t_stop = time.perf_counter()
 
     def stop(self) -> dict | None:
         if self.proc is None:
             return None
+        if self.t_stop is None:
+            self.mark_stop()
+        time.sleep(self.INTERVAL_MS * 1.5e-3)          # the reading that covers the end
         self.proc.terminate()
         try:
             self.proc.wait(timeout=5)
         except subprocess.TimeoutExpired:
             self.proc.kill()
         self._t.join(timeout=2)
+        lo = self.t_start if self.t_start is not None else 0.0
+        hi = self.t_stop + self.INTERVAL_MS * 1.5e-3
+        window = [line for t, line in self.lines if lo <= t <= hi]
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for line in self.lines:
+        for line in window:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -491,6 +512,9 @@ def run_ours(args, world, rank, local):
                 batch.accumulate(integration(k), stream=stream)
                 batch.dump(outs[k & 1], stream=stream)
 
+    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clocks:
+        clocks.start()           # before the warm-up: nvidia-smi is slow to produce its first reading
     with torch.cuda.stream(stream):
         for _ in range(args.warmup):
             step()
@@ -498,11 +522,10 @@ def run_ours(args, world, rank, local):
     batch.profile_read(reset=True)
     if args.mode == "direct":
         batch.profile_enable(True)
-    clocks = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
     barrier(world)
     torch.cuda.synchronize(dev)
     if clocks:
-        clocks.start()
+        clocks.mark_start()
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for st in range(args.steps):
@@ -510,6 +533,8 @@ def run_ours(args, world, rank, local):
         step(timed=(args.mode == "graph" and st == args.steps - 1))
     ev1.record(stream)
     torch.cuda.synchronize(dev)
+    if clocks:
+        clocks.mark_stop()
     barrier(world)
     clk = clocks.stop() if clocks else None
     batch.sync(stream)
