@@ -130,3 +130,36 @@ def test_fine_pfb_argument_errors():
     v, _ = corr.fine_pfb(x, h)
     torch.cuda.synchronize()
     assert v.shape == (1, 128, 8) and int(v.sum()) == 0
+
+
+@pytest.mark.parametrize("taps", [1, 12])
+def test_fine_pfb_output_choices(taps):
+    """Spectra only, codes only, and both into caller tensors agree with each
+    other and with the oracle; 13 inputs leave a partial group of 8, whose
+    codes go out byte by byte."""
+    Q, N, M = 2, 13, 9
+    S = 128 * (M + taps - 1)
+    x = coarse.coarse_samples(900 + taps, Q, N, S, sigma=12.0)
+    h = coarse.kaiser_sinc_window(taps) if taps > 1 else np.ones(128)
+    scale = coarse.output_scale(h, 12.0)
+    xt = torch.from_numpy(x).cuda()
+    ht = torch.from_numpy(h.astype(np.float32)).cuda()
+    v_only, none = corr.fine_pfb(xt, ht, scale, volt=True, spec=False)
+    assert none is None
+    none2, s_only = corr.fine_pfb(xt, ht, scale, volt=False, spec=True)
+    assert none2 is None
+    v_out = torch.full((M, Q * 128, N), 0xAB, dtype=torch.uint8, device="cuda")
+    s_out = torch.full((M, Q * 128, N, 2), float("nan"), dtype=torch.float32, device="cuda")
+    v_both, s_both = corr.fine_pfb(xt, ht, scale, volt=v_out, spec=s_out)
+    torch.cuda.synchronize()
+    assert v_both is v_out and s_both is s_out
+    assert torch.equal(v_only, v_out) and torch.equal(s_only, s_out)
+    h64 = h.astype(np.float32).astype(np.float64)
+    want_spec, _ = oracle.fine_pfb(x, h64, scale)
+    got = s_out.cpu().numpy()
+    err = np.abs(got[..., 0] + 1j * got[..., 1] - want_spec)
+    b = _bound(x, h64)
+    assert (err <= b).all()
+    _check_codes(v_out.cpu().numpy(), want_spec, b, scale)
+    with pytest.raises(ValueError):
+        corr.fine_pfb(xt, ht, scale, volt=False, spec=False)
