@@ -27,6 +27,19 @@ are integrated on the GPU for an operator-chosen time before being copied out
   GPU work that correlated it; the report gives p50/p99 latency and the
   x-real-time margin (tick period / GPU time per tick).
 
+Two ways to correlate (``mode``):
+
+* ``"block"`` (default): every block is added to the array's running
+  integration as it arrives, so its latency is one block's copy and
+  correlation;
+* ``"dump"``: the blocks of an integration wait in a device ring of
+  ``blocks_per_dump`` slots and are correlated together, as one whole
+  integration written straight into the dump buffer, when the last one has
+  arrived -- the paper's own arrangement (one GPU launch per input block of a
+  second, Section 3.4.1).  A block then waits up to one integration, but the
+  GPU does a single fresh pass per integration instead of adding every block
+  into the accumulators.
+
 The GPU side lives behind a small backend interface so that the control logic
 can be exercised without a GPU (tests/test_service.py uses a fake backend).
 """
@@ -152,7 +165,14 @@ class Source(threading.Thread):
 
 class Service:
     def __init__(self, specs, hbm_budget: int, backend, ring_blocks: int = 3,
-                 paced: bool = True, stall_s: float = 1.0, max_queue: int = 8):
+                 paced: bool = True, stall_s: float = 1.0, max_queue: int = 8, mode: str = "block"):
+        if mode not in ("block", "dump"):
+            raise ValueError("mode is 'block' or 'dump'")
+        self.mode = mode
+        if mode == "dump":
+            # a ring slot per block of an integration
+            ring_blocks = max([ring_blocks] + [s.blocks_per_dump for s in specs])
+        backend.per_dump = mode == "dump"
         self.backend = backend
         self.ring_blocks = ring_blocks
         self.paced = paced
@@ -179,6 +199,8 @@ class Service:
             src.start()
         expected = [0] * len(specs)
         in_dump = [[] for _ in specs]
+        in_dump_arrivals = [[] for _ in specs]
+        per_dump = self.mode == "dump"
         tainted = [False] * len(specs)
         last_arrival = [t0] * len(specs)
         stalled = [False] * len(specs)
@@ -228,15 +250,22 @@ class Service:
                 expected[a] = blk.seq + 1
                 rooms[a].release()
             handle = self.backend.submit({a: blk for a, blk in got.items()})
-            completer_q.put((handle, [(a, blk.arrival) for a, blk in got.items()]))
+            if not per_dump:
+                completer_q.put((handle, [(a, blk.arrival) for a, blk in got.items()]))
             due = []
             for a, blk in got.items():
                 self.stats[a].blocks += 1
                 in_dump[a].append(blk.seq)
+                in_dump_arrivals[a].append(blk.arrival)
                 if len(in_dump[a]) == specs[a].blocks_per_dump:
                     due.append(a)
             if due:
                 h = self.backend.dump(due)
+                if per_dump:
+                    # the blocks of these integrations are correlated by this dump
+                    completer_q.put((h, [(a, arr) for a in due for arr in in_dump_arrivals[a]]))
+                for a in due:
+                    in_dump_arrivals[a] = []
                 for a in due:
                     self.dumps.append((a, self.stats[a].dumps, list(in_dump[a]), tainted[a], h))
                     self.stats[a].dumps += 1
@@ -267,7 +296,9 @@ class Service:
                 "stalls": st.stalls, "failed": st.failed,
                 "p50_ms": _pct(lat, 50), "p99_ms": _pct(lat, 99)})
         all_lat.sort()
-        period = min((s.period_s for s in self.admitted), default=0.0)
+        # the GPU work is timed per tick (block mode) or per integration (dump mode)
+        period = min(((s.period_s * (s.blocks_per_dump if self.mode == "dump" else 1))
+                      for s in self.admitted), default=0.0)
         gpu = statistics.median(self.tick_gpu_ms) if self.tick_gpu_ms else None
         data_s = max((st.blocks * s.period_s for s, st in zip(self.admitted, self.stats)), default=0.0)
         return {
@@ -277,8 +308,10 @@ class Service:
             "p50_ms": _pct(all_lat, 50), "p99_ms": _pct(all_lat, 99),
             "gpu_ms_per_tick_median": gpu,
             "x_real_time_margin": (period * 1e3 / gpu) if gpu else None,
-            "margin_note": "tick period / median GPU correlation time per tick (copies excluded); "
-                           "x_real_time_wall = data seconds / wall seconds (copies included)",
+            "margin_note": ("tick period / median GPU correlation time per tick" if self.mode == "block" else
+                            "integration period / median GPU correlation time per integration") +
+                           " (copies excluded); x_real_time_wall = data seconds / wall seconds (copies included)",
+            "mode": self.mode,
             "x_real_time_wall": (data_s / wall_s) if wall_s > 0 else None,
             "wall_s": wall_s, "paced": self.paced,
         }
@@ -293,6 +326,8 @@ def _pct(sorted_vals, p):
 
 class GpuBackend:
     """The GPU side: device rings, one batched correlator, dump buffers."""
+
+    per_dump = False      # set by Service: correlate whole integrations at dump time
 
     def __init__(self, device=None, pool_blocks: int = 2, path: str = "auto",
                  verify_channels: int = 2):
@@ -357,6 +392,10 @@ class GpuBackend:
         torch.cuda.synchronize(self.device)
         self.batch.accumulate([r[0] for r in self.rings], stream=self.compute)
         self.batch.dump([v[0] for v in self.vis], stream=self.compute)
+        if self.per_dump:
+            self.batch.integrate([r[:sp.blocks_per_dump].view(-1, sp.n_chan, sp.n_inputs)
+                                  for r, sp in zip(self.rings, self.specs)],
+                                 [v[0] for v in self.vis], stream=self.compute)
         self.compute.synchronize()
         for a in range(len(self.specs)):
             with torch.cuda.stream(self.d2h_stream):
@@ -366,6 +405,10 @@ class GpuBackend:
     def host_block(self, a, k):
         return self.pool[a][k % self.pool_blocks]
 
+    def _slot(self, a, seq):
+        # in dump mode the slots of one integration hold its blocks in order
+        return seq % (self.specs[a].blocks_per_dump if self.per_dump else self.ring_blocks)
+
     def submit(self, blocks: dict):
         torch = self.torch
         ptrs = [None] * len(self.specs)
@@ -373,7 +416,7 @@ class GpuBackend:
         end = torch.cuda.Event(enable_timing=True)
         copied = torch.cuda.Event()
         for a, blk in blocks.items():
-            slot = blk.seq % self.ring_blocks
+            slot = self._slot(a, blk.seq)
             free = self.slot_free[a][slot]
             if free is not None:
                 self.copy_stream.wait_event(free)
@@ -381,12 +424,15 @@ class GpuBackend:
                 self.rings[a][slot].copy_(blk.data, non_blocking=True)
             ptrs[a] = self.rings[a][slot]
         copied.record(self.copy_stream)
+        if self.per_dump:
+            self.copied = copied           # the dump waits for the last copies
+            return None
         self.compute.wait_event(copied)
         start.record(self.compute)
         self.batch.accumulate(ptrs, stream=self.compute)
         end.record(self.compute)
         for a, blk in blocks.items():
-            self.slot_free[a][blk.seq % self.ring_blocks] = end
+            self.slot_free[a][self._slot(a, blk.seq)] = end
         return (start, end)
 
     def dump(self, arrays):
@@ -397,7 +443,24 @@ class GpuBackend:
             if self.d2h_done[a][slot] is not None:   # the copy out of this buffer has finished
                 self.compute.wait_event(self.d2h_done[a][slot])
             outs[a] = self.vis[a][slot]
-        self.batch.dump(outs, stream=self.compute)
+        handle = None
+        if self.per_dump:
+            # the whole integration from the ring, written straight into the dump buffer
+            volts = [None] * len(self.specs)
+            for a in arrays:
+                sp = self.specs[a]
+                volts[a] = self.rings[a][:sp.blocks_per_dump].view(-1, sp.n_chan, sp.n_inputs)
+            self.compute.wait_event(self.copied)
+            start = torch.cuda.Event(enable_timing=True)
+            end = torch.cuda.Event(enable_timing=True)
+            start.record(self.compute)
+            self.batch.integrate(volts, outs, stream=self.compute)
+            end.record(self.compute)
+            for a in arrays:
+                self.slot_free[a] = [end] * self.ring_blocks
+            handle = (start, end)
+        else:
+            self.batch.dump(outs, stream=self.compute)
         done = torch.cuda.Event()
         done.record(self.compute)
         self.d2h_stream.wait_event(done)
@@ -415,7 +478,7 @@ class GpuBackend:
             self.d2h_done[a][slot] = ev
             self.kept.append((a, self.dump_count[a], rows))
             self.dump_count[a] += 1
-        return done
+        return handle if self.per_dump else done
 
     def wait(self, handle):
         start, end = handle
@@ -434,11 +497,14 @@ def main(argv=None):
     ap.add_argument("--unpaced", action="store_true", help="deliver blocks as fast as accepted")
     ap.add_argument("--hbm-budget-gb", type=float, default=64.0)
     ap.add_argument("--channels", type=int, default=3072)
+    ap.add_argument("--mode", choices=("block", "dump"), default="block",
+                    help="block: add every block as it arrives; dump: correlate each integration "
+                         "as one launch when its last block has arrived")
     args = ap.parse_args(argv)
     specs = [StreamSpec("mwa256", 256, args.channels, array=0),
              StreamSpec("aux128", 128, args.channels, array=1),
              StreamSpec("aux512", 512, args.channels, array=2)]
-    svc = Service(specs, int(args.hbm_budget_gb * 1e9), GpuBackend(), paced=not args.unpaced)
+    svc = Service(specs, int(args.hbm_budget_gb * 1e9), GpuBackend(), paced=not args.unpaced, mode=args.mode)
     n_blocks = int(round(args.seconds / specs[0].period_s))
     print(json.dumps(svc.run(n_blocks)))
 

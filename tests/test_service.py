@@ -98,3 +98,29 @@ def test_paced_latency_is_measured_from_real_time_arrival():
     a = rep["arrays"][0]
     assert a["blocks"] == 6
     assert 0.5 < a["p50_ms"] < 200
+
+
+class FakeDumpBackend(FakeBackend):
+    """As FakeBackend; records which blocks each dump correlates."""
+
+    def dump(self, arrays):
+        self.dumps.append(list(arrays))
+        return ("dump", tuple(arrays))
+
+
+def test_dump_mode_times_whole_integrations():
+    be = FakeDumpBackend(gpu_ms=1.0)
+    svc = Service(SPECS, 1 << 40, be, paced=False, mode="dump")
+    assert be.per_dump and svc.ring_blocks == 4
+    rep = svc.run(8)
+    assert rep["mode"] == "dump"
+    for a in rep["arrays"]:
+        assert a["blocks"] == 8 and a["dumps"] == 2 and a["gaps"] == 0
+    # latencies are recorded when the dump that correlates a block completes:
+    # one per block, timed once per dump call (the arrays' dumps fall in the
+    # same call when their blocks arrive together, else in separate ones)
+    assert 2 <= len(svc.tick_gpu_ms) <= 6
+    assert sum(len(st.latencies_ms) for st in svc.stats) == 3 * 8
+    assert abs(rep["x_real_time_margin"] - 4 * SPECS[0].period_s * 1e3 / 1.0) < 1e-9
+    with pytest.raises(ValueError):
+        Service(SPECS, 1 << 40, FakeBackend(), mode="tick")

@@ -11,13 +11,13 @@ from paper_1501_05992_gb300.service import GpuBackend, Service, StreamSpec
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("paced", [False, True])
-def test_service_dumps_are_exact(paced):
+@pytest.mark.parametrize("paced,mode", [(False, "block"), (True, "block"), (False, "dump"), (True, "dump")])
+def test_service_dumps_are_exact(paced, mode):
     specs = [StreamSpec("a256", 256, 12, block_samples=500, blocks_per_dump=4, array=0),
              StreamSpec("a128", 128, 20, block_samples=500, blocks_per_dump=4, array=1),
              StreamSpec("a64", 64, 9, block_samples=500, blocks_per_dump=4, array=2)]
     be = GpuBackend(pool_blocks=3, verify_channels=3)
-    svc = Service(specs, 1 << 36, be, paced=paced)
+    svc = Service(specs, 1 << 36, be, paced=paced, mode=mode)
     rep = svc.run(8)
     for a in rep["arrays"]:
         assert a["blocks"] == 8 and a["dumps"] == 2 and a["gaps"] == 0, a
