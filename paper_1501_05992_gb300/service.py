@@ -377,6 +377,7 @@ class GpuBackend:
                 d = gen.make(k * s.block_samples, s.block_samples)
                 blocks.append(d.cpu().pin_memory())
             self.pool.append(blocks)
+        self.copied = None                                    # last block copies (dump mode)
         self.copy_stream = torch.cuda.Stream(self.device)     # host -> device blocks
         self.d2h_stream = torch.cuda.Stream(self.device)      # dumps -> host, so that block
         self.compute = torch.cuda.Stream(self.device)         # uploads never queue behind them
@@ -450,7 +451,8 @@ class GpuBackend:
             for a in arrays:
                 sp = self.specs[a]
                 volts[a] = self.rings[a][:sp.blocks_per_dump].view(-1, sp.n_chan, sp.n_inputs)
-            self.compute.wait_event(self.copied)
+            if self.copied is not None:
+                self.compute.wait_event(self.copied)
             start = torch.cuda.Event(enable_timing=True)
             end = torch.cuda.Event(enable_timing=True)
             start.record(self.compute)
