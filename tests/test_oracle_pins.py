@@ -1,7 +1,6 @@
 """The CPU oracle against its pins, and the pins against planted mistakes."""
 import os
 import re
-import tempfile
 
 import numpy as np
 import pytest
