@@ -401,7 +401,35 @@ def measure_extras(arrays, volts, outs, stream_, dev, peaks, src):
                             "peak_gbs": hbm, "bound": "hbm"}
     if n % 8 == 0 and f % 128 == 0:
         res["fine_pfb"] = measure_fine_pfb(n, f // 128, t, stream_, dev)
+    res["cudacore_vs_tc"] = measure_cudacore_vs_tc(n, f, t, volt, stream_, dev)
     return res
+
+
+def measure_cudacore_vs_tc(n, f, t, volt, stream_, dev):
+    """The same integration through the CUDA-core (dp4a) X-engine and the
+    tcgen05 one, each as a whole-integration call: time per integration,
+    CMAC/s, and whether the two triangles are identical (both must be exact)."""
+    import torch
+    from paper_1501_05992_gb300 import corr
+    out = {}
+    tri = {}
+    for path in ("cudacore", "tc_fp8"):
+        try:
+            c = corr.Correlator(n, f, t, path=path, device=dev)
+        except corr.CorrError:
+            out[path] = None
+            continue
+        dst = torch.empty((f, n * (n + 1) // 2, 2), dtype=torch.int32, device=dev)
+        ms = _time_ms(lambda: c.integrate(volt, dst, stream=stream_), stream_, reps=3)
+        c.close()
+        tri[path] = dst
+        cmac = n * (n + 1) // 2 * f * t
+        out[path] = {"ms_per_integration": ms, "value": cmac / (ms * 1e-3), "unit": "CMAC/s",
+                     "x_real_time": t / SAMPLE_RATE_HZ / (ms * 1e-3)}
+    if out.get("cudacore") and out.get("tc_fp8"):
+        out["tc_speedup"] = out["cudacore"]["ms_per_integration"] / out["tc_fp8"]["ms_per_integration"]
+        out["identical"] = bool(torch.equal(tri["cudacore"], tri["tc_fp8"]))
+    return out
 
 
 FP32_LANES_PER_SM = 128          # fp32 FMA lanes per SM (4 sub-partitions x 32)
