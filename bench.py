@@ -14,7 +14,11 @@ corr_batch_accumulate + corr_batch_dump per integration.
 Prints one JSON line (rank 0).  `value` is device-resident throughput, `e2e`
 the same metric through the host-buffer C-ABI calls (host->device copies of
 every step's voltages and device->host copies of every dump inside the timed
-region).  `--impl reference` times the CPU oracle on a bounded sample instead.
+region).  After the timed region, rank 0 adds `extras`: the incoherent beam,
+packet ingest, output remap and fine filterbank with their rooflines, and the
+CUDA-core X-engine against the tensor-core one on the same integration
+(times and whether the triangles are identical).  `--impl reference` times
+the CPU oracle on a bounded sample instead.
 """
 from __future__ import annotations
 
