@@ -163,3 +163,30 @@ def test_fine_pfb_output_choices(taps):
     _check_codes(v_out.cpu().numpy(), want_spec, b, scale)
     with pytest.raises(ValueError):
         corr.fine_pfb(xt, ht, scale, volt=False, spec=False)
+
+
+def test_fine_pfb_full_scale_inputs():
+    """Samples at the ends of the int8 range (random +-127 and -128, and runs of
+    a constant full-scale value, whose whole power lands in channel 64): the
+    largest spectra the format allows stay within the fp32 bound, and the
+    codes saturate at +-7 exactly where the oracle's do."""
+    Q, N, M, taps = 1, 16, 40, 12
+    S = 128 * (M + taps - 1)
+    rng = np.random.default_rng(127)
+    x = rng.choice(np.array([-128, -127, 127], np.int8), size=(Q, N, S, 2))
+    x[0, 3] = 127                                   # DC at full scale
+    x[0, 4, :, 0] = -128
+    x[0, 4, :, 1] = 127
+    h = coarse.kaiser_sinc_window(taps)
+    h64 = h.astype(np.float32).astype(np.float64)
+    scale = coarse.output_scale(h, 127.0)
+    want_spec, want_volt = oracle.fine_pfb(x, h64, scale)
+    got_volt, got_spec = _run(x, h, scale)
+    b = _bound(x, h64)
+    err = np.abs(got_spec[..., 0] + 1j * got_spec[..., 1] - want_spec)
+    assert (err <= b).all(), f"max error / bound {np.max(err / b):.3f}"
+    _check_codes(got_volt, want_spec, b, scale)
+    # the constant inputs saturate channel 64 and leave the rest near zero
+    vals = np.array([v if v < 8 else v - 16 for v in range(16)])
+    assert np.all(vals[got_volt[:, 64, 3] >> 4] == 7) and np.all(vals[got_volt[:, 64, 3] & 15] == 7)
+    assert np.all(vals[got_volt[:, 64, 4] >> 4] == -7) and np.all(vals[got_volt[:, 64, 4] & 15] == 7)
