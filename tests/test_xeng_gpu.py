@@ -320,7 +320,7 @@ def test_many_channels_and_tiles(path):
 # 4 tiles with a ragged last tile, and each is run as one long fresh launch
 # (pairs), as a short fresh launch followed by a long accumulating one (pairs
 # adding into the output), and as launches of 1000 samples (single items).
-PAIR_SHAPES = [(130, 2, 4097), (256, 7, 4100), (272, 3, 4160), (400, 2, 4160)]
+PAIR_SHAPES = [(144, 2, 4097), (256, 7, 4100), (272, 3, 4160), (400, 2, 4160)]
 
 
 @pytest.mark.parametrize("shape", PAIR_SHAPES, ids=lambda s: "N%d_F%d_T%d" % s)
@@ -349,3 +349,19 @@ def test_tc_pair_items_many_channels():
     chans = [0, 1, 151, 152, 153, 303, 304, 330]
     want = oracle.to_int32(oracle.xmac(np.ascontiguousarray(volt[:, chans])))
     assert np.array_equal(got[chans], want)
+
+
+def test_tc_pair_items_zero_invalid():
+    """Pair items (a long fresh launch) with the invalid-code reading on: every
+    sample with a nibble of 8 counts as zero, in the diagonal and the off-
+    diagonal part of each pair alike."""
+    N, F, T = 256, 3, 4160
+    if not path_available("tc_fp8", N):
+        pytest.skip("tc_fp8 unsupported")
+    rng = np.random.default_rng(88)
+    volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    volt.reshape(-1)[::7] = 0x88
+    volt.reshape(-1)[3::11] = 0x38
+    want = oracle.to_int32(oracle.xmac(volt, zero_invalid=True))
+    assert np.array_equal(correlate(volt, "tc_fp8", zero_invalid=True), want)
+    assert not np.array_equal(correlate(volt, "tc_fp8"), want)      # the reading matters here
