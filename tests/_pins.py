@@ -503,6 +503,31 @@ def pin_fpfb_paper_structure(o):
     assert spec.shape == volt.shape == (5, 2 * L, 1), "frames and channels of a 12-tap, 128-point bank"
 
 
+def pin_fpfb_feeds_xmac(o):
+    """F then X: inputs carrying integer tones at bin 32 with complex
+    amplitudes A_n, through the flat 12-tap window and scale 1/128, become the
+    codes A_n in channel 96 of every frame (0 elsewhere), so correlating the M
+    frames gives V_ij = M A_i conj(A_j) in channel 96 and zero in every other
+    channel: the filterbank's output layout is the correlator's input layout."""
+    taps, M, N = 12, 6, 4
+    S = 128 * (M + taps - 1)
+    s = np.arange(S)
+    amps = [3 + 1j, -2 + 2j, 1 - 3j, -1 - 1j]
+    x = np.zeros((1, N, S, 2), np.int8)
+    for n, a in enumerate(amps):
+        z = a * (1j ** s)
+        x[0, n, :, 0] = np.rint(z.real)
+        x[0, n, :, 1] = np.rint(z.imag)
+    _, codes = o.fine_pfb(x, np.full(taps * 128, 1.0 / taps), 1.0 / 128)
+    vis = o.xmac(codes)                                     # [128][P][2]
+    want = np.zeros_like(vis)
+    for i in range(N):
+        for j in range(i + 1):
+            v = M * amps[i] * np.conj(amps[j])
+            want[96, tri_index(i, j)] = (round(v.real), round(v.imag))
+    assert np.array_equal(vis, want), "filterbank codes must feed the correlator in its input layout"
+
+
 ALL_PINS = [pin_decode_table, pin_library_matmul, pin_hermitian, pin_autos,
             pin_constant_closed_form, pin_rank_one, pin_additivity, pin_permutation,
             pin_tone_phase, pin_invalid_reading, pin_paper_sizes, pin_brute_force,
@@ -510,4 +535,4 @@ ALL_PINS = [pin_decode_table, pin_library_matmul, pin_hermitian, pin_autos,
             pin_remap_natural_order, pin_remap_paper_count, pin_ingest_golden_packet,
             pin_ingest_rejections, pin_ingest_round_trip, pin_fpfb_single_tap_is_library_fft,
             pin_fpfb_impulse_response, pin_fpfb_tones, pin_fpfb_frame_shift, pin_fpfb_quantiser,
-            pin_fpfb_paper_structure]
+            pin_fpfb_paper_structure, pin_fpfb_feeds_xmac]
