@@ -15,10 +15,13 @@ Prints one JSON line (rank 0).  `value` is device-resident throughput, `e2e`
 the same metric through the host-buffer C-ABI calls (host->device copies of
 every step's voltages and device->host copies of every dump inside the timed
 region).  After the timed region, rank 0 adds `extras`: the incoherent beam,
-packet ingest, output remap and fine filterbank with their rooflines, and the
-CUDA-core X-engine against the tensor-core one on the same integration
-(times and whether the triangles are identical).  `--impl reference` times
-the CPU oracle on a bounded sample instead.
+packet ingest, output remap and fine filterbank with their rooflines; the
+dp4a CUDA-core, int8 mma.sync and tcgen05 FP8 X-engines on the same
+integration (times, fractions of their rooflines, identical triangles, oracle
+check); the uneven three-array batch in one persistent launch with
+autotuned paths; and the streaming service of three arrays, paced and
+unpaced, with every dump checked against the oracle on sampled channels.
+`--impl reference` times the CPU oracle on a bounded sample instead.
 """
 from __future__ import annotations
 
@@ -264,6 +267,10 @@ def run_reference(args, world, rank):
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": step_cmac / value * 1e3, "higher_is_better": True,
+        "ms_per_step_note": ("extrapolated: each timed step runs the oracle on a bounded channel "
+                             "sample of the workload, and ms_per_step is the whole step's "
+                             "CMAC divided by the median sampled rate"),
+        "sampled": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "int64", "data": "synthetic",
         "x_real_time": value / rt_rate,
         "config": workload_config(args, ["oracle (CPU, int64 triple loop)"]),
@@ -320,10 +327,13 @@ def measured_traffic(kernel_src: str, profile_md: str, workload: str):
 def roofline_for(path, ops_per_launch, avg_ms, peaks, src, sm_count):
     achieved = ops_per_launch / (avg_ms * 1e-3) / 1e12          # Tops/s
     if path == "tc_fp8":
-        peak = peaks["bf16_tflops_sustained"] * 2.0              # fp8 = 2 x bf16 (nominal ratio)
+        # fp8 dense = 2 x bf16 (the nominal ratio) x the measured bf16 burst
+        # rate: the X-engine launch lasts about 2 ms, far shorter than the
+        # seconds-long loop the sustained figure comes from
+        peak = peaks["bf16_tflops"] * 2.0
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak,
-                "peak_note": f"fp8 dense = 2 x bf16 sustained ({src}); ops = 8 per useful CMAC"}
+                "peak_note": f"fp8 dense = 2 x bf16 burst ({src}); ops = 8 per useful CMAC"}
     if path == "mma_i8":
         # int8 tensor rates on this part are far below 2 x bf16; the peak is
         # the measured rate of back-to-back mma.sync m16n8k32 s8 in registers
@@ -358,13 +368,15 @@ def _time_ms(fn, stream, reps=5):
     return statistics.median(ts)
 
 
-def measure_extras(arrays, volts, outs, stream_, dev, peaks, src):
+def measure_extras(arrays, volts, outs, stream_, dev, peaks, src, full=True):
     """The stages around the X-engine on the first array's first integration,
     against the HBM roofline: the incoherent beam (reads every voltage byte
     once, writes one int32 per channel and sample), the packet ingest of one
     50 ms bank (reads the packets, writes the voltage block) and the output
     remap with 2 x 2 averaging (reads two dumps' triangles, writes the
-    station-order products of channel pairs).  Not part of the timed step."""
+    station-order products of channel pairs).  Then the three X-engine forms
+    on the same integration; with `full`, the uneven batch and the streaming
+    service too.  Not part of the timed step."""
     import torch
     from paper_1501_05992_gb300 import corr
     n, f, t = arrays[0]
@@ -405,19 +417,36 @@ def measure_extras(arrays, volts, outs, stream_, dev, peaks, src):
                             "peak_gbs": hbm, "bound": "hbm"}
     if n % 8 == 0 and f % 128 == 0:
         res["fine_pfb"] = measure_fine_pfb(n, f // 128, t, stream_, dev)
-    res["cudacore_vs_tc"] = measure_cudacore_vs_tc(n, f, t, volt, stream_, dev)
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    res["paths_one_integration"] = measure_paths(n, f, t, volt, stream_, dev, peaks, sm_count)
+    torch.cuda.empty_cache()
+    if full:
+        res["uneven_batch"] = measure_uneven_batch(stream_, dev, peaks, sm_count)
+        torch.cuda.empty_cache()
+        res["service"] = measure_service(dev)
+        torch.cuda.empty_cache()
     return res
 
 
-def measure_cudacore_vs_tc(n, f, t, volt, stream_, dev):
-    """The same integration through the CUDA-core (dp4a) X-engine and the
-    tcgen05 one, each as a whole-integration call: time per integration,
-    CMAC/s, and whether the two triangles are identical (both must be exact)."""
+def _oracle_channels(volt_dev, chans):
+    """Oracle triangles (int32) of whole channels of a device voltage block."""
+    import oracle
+    sub = volt_dev[:, chans].cpu().numpy()
+    return oracle.to_int32(oracle.xmac(sub))
+
+
+def measure_paths(n, f, t, volt, stream_, dev, peaks, sm_count):
+    """The same integration through the three X-engine forms, each as a
+    whole-integration call: the dp4a CUDA-core kernel, the int8 mma.sync
+    kernel and the tcgen05 FP8 kernel.  Time per integration, CMAC/s, the
+    fraction of each form's own roofline, whether the three triangles are
+    identical, and whether they equal the oracle on four whole channels."""
     import torch
     from paper_1501_05992_gb300 import corr
     out = {}
     tri = {}
-    for path in ("cudacore", "tc_fp8"):
+    cmac = n * (n + 1) // 2 * f * t
+    for path in ("cudacore", "mma_i8", "tc_fp8"):
         try:
             c = corr.Correlator(n, f, t, path=path, device=dev)
         except corr.CorrError:
@@ -425,14 +454,129 @@ def measure_cudacore_vs_tc(n, f, t, volt, stream_, dev):
             continue
         dst = torch.empty((f, n * (n + 1) // 2, 2), dtype=torch.int32, device=dev)
         ms = _time_ms(lambda: c.integrate(volt, dst, stream=stream_), stream_, reps=3)
+        c.sync(stream_)
         c.close()
         tri[path] = dst
-        cmac = n * (n + 1) // 2 * f * t
+        roof = roofline_for(path, 8.0 * cmac, ms, peaks, "measured", sm_count)
         out[path] = {"ms_per_integration": ms, "value": cmac / (ms * 1e-3), "unit": "CMAC/s",
-                     "x_real_time": t / SAMPLE_RATE_HZ / (ms * 1e-3)}
+                     "x_real_time": t / SAMPLE_RATE_HZ / (ms * 1e-3),
+                     "achieved": roof["achieved"], "peak": roof["peak"], "frac": roof["frac"],
+                     "peak_unit": roof["unit"], "peak_note": roof["peak_note"]}
+    have = [p for p in ("cudacore", "mma_i8", "tc_fp8") if out.get(p)]
     if out.get("cudacore") and out.get("tc_fp8"):
         out["tc_speedup"] = out["cudacore"]["ms_per_integration"] / out["tc_fp8"]["ms_per_integration"]
-        out["identical"] = bool(torch.equal(tri["cudacore"], tri["tc_fp8"]))
+    if out.get("mma_i8") and out.get("tc_fp8"):
+        out["fp8_vs_int8_speedup"] = out["mma_i8"]["ms_per_integration"] / out["tc_fp8"]["ms_per_integration"]
+    out["identical"] = all(bool(torch.equal(tri[have[0]], tri[p])) for p in have[1:])
+    chans = sorted({0, 1, f // 2, f - 1})
+    want = _oracle_channels(volt, chans)
+    out["exact"] = bool(out["identical"]) and all(
+        bool((tri[p][chans].cpu().numpy() == want).all()) for p in have)
+    out["exact_note"] = (f"the {len(have)} triangles are compared element by element over all "
+                         f"{f} channels, and against the oracle on whole channels {chans}")
+    del tri
+    return out
+
+
+def measure_uneven_batch(stream_, dev, peaks, sm_count):
+    """The uneven batch (three arrays of 128, 256 and 1024 inputs) correlated
+    in one persistent launch, each array's path chosen by the autotuner:
+    whole-batch and per-array throughput, and whole triangles of two channels
+    of every array against the oracle (the 1024-input array at its full
+    10000 samples)."""
+    import tempfile
+
+    import torch
+    from paper_1501_05992_gb300 import autotune, corr
+    from synth import voltgen as vg
+    from synth.gpu import DeviceGenerator
+    arrays, _, seed = WORKLOADS["uneven_batch"]
+    volts = [DeviceGenerator(vg.gauss3_params(seed, n, f, array=a), dev).make(0, t)
+             for a, (n, f, t) in enumerate(arrays)]
+    cache = os.path.join(tempfile.gettempdir(), "corr_autotune_bench.json")
+    specs = autotune.plan([{"n_inputs": n, "n_chan": f, "n_time_per_int": t} for n, f, t in arrays],
+                          cache_path=cache)
+    tuned = [autotune.tune(n, f, t, cache_path=cache) for n, f, t in arrays]
+    batch = corr.Batch(specs, device=dev)
+    outs = batch._outs(None)
+    ms_all = _time_ms(lambda: batch.integrate(volts, outs, stream=stream_), stream_, reps=5)
+    batch.sync(stream_)
+    res = {"arrays": [], "paths": batch.paths, "autotune_cache": cache}
+    cmac_all = 0
+    for a, ((n, f, t), spec) in enumerate(zip(arrays, specs)):
+        cmac = n * (n + 1) // 2 * f * t
+        cmac_all += cmac
+        one = corr.Batch([spec], device=dev)
+        o1 = one._outs(None)
+        ms = _time_ms(lambda: one.integrate([volts[a]], o1, stream=stream_), stream_, reps=3)
+        one.sync(stream_)
+        same = bool(torch.equal(o1[0], outs[a]))
+        one.close()
+        del o1
+        chans = [0, f - 1]
+        exact = bool((outs[a][chans].cpu().numpy() == _oracle_channels(volts[a], chans)).all())
+        roof = roofline_for(spec["path"], 8.0 * cmac, ms, peaks, "measured", sm_count)
+        res["arrays"].append({
+            "n_inputs": n, "n_chan": f, "samples": t, "path": spec["path"], "tile": spec["tile"],
+            "autotune_ms": tuned[a]["ms"], "ms_alone": ms, "value_alone": cmac / (ms * 1e-3),
+            "frac_alone": roof["frac"], "same_as_in_batch": same, "exact": exact,
+            "exact_channels": chans})
+    roof = roofline_for("tc_fp8" if all(p == "tc_fp8" for p in batch.paths) else batch.paths[0],
+                        8.0 * cmac_all, ms_all, peaks, "measured", sm_count)
+    res.update({"ms_batch": ms_all, "value": cmac_all / (ms_all * 1e-3), "unit": "CMAC/s",
+                "achieved": roof["achieved"], "peak": roof["peak"], "frac": roof["frac"],
+                "exact": all(x["exact"] and x["same_as_in_batch"] for x in res["arrays"]),
+                "launch": "one corr_batch_integrate: the tensor-core arrays share one persistent launch"})
+    batch.close()
+    del volts, outs
+    return res
+
+
+def measure_service(dev, seconds: float = 10.0):
+    """The streaming service of three arrays (256, 128 and 512 inputs x 3072
+    channels, 50 ms blocks of 500 samples, 0.5 s dumps): one run paced to
+    real time for `seconds` and one run of the same data delivered as fast as
+    the service accepts it.  Every dump is checked against the oracle on
+    sampled channels, its blocks regenerated from the seeded generator."""
+    import numpy as np
+    import oracle
+    from paper_1501_05992_gb300.service import GpuBackend, Service, StreamSpec
+    from synth import voltgen as vg
+    specs = [StreamSpec("mwa256", 256, 3072, array=0), StreamSpec("aux128", 128, 3072, array=1),
+             StreamSpec("aux512", 512, 3072, array=2)]
+    n_blocks = int(round(seconds / specs[0].period_s))
+    expected = {}
+
+    def want(spec, pool_blocks, f, seqs):
+        key = (spec.name, f, tuple(q % pool_blocks for q in seqs))
+        if key not in expected:
+            params = vg.gauss3_params(spec.seed, spec.n_inputs, spec.n_chan, array=spec.array)
+            block = np.concatenate([vg.gauss3(params, (q % pool_blocks) * spec.block_samples,
+                                              spec.block_samples, f, 1) for q in seqs])
+            expected[key] = oracle.to_int32(oracle.xmac(block))[0]
+        return expected[key]
+
+    out = {}
+    for label, paced in (("paced", True), ("unpaced", False)):
+        import torch
+        free, _ = torch.cuda.mem_get_info(dev)
+        be = GpuBackend(device=dev.index or 0, pool_blocks=2, verify_channels=2)
+        svc = Service(specs, int(free * 0.9), be, paced=paced, mode="block")
+        rep = svc.run(n_blocks)
+        checked = bad = 0
+        for a, d, rows in be.kept:
+            spec = specs[a]
+            seqs = list(range(d * spec.blocks_per_dump, (d + 1) * spec.blocks_per_dump))
+            for f, got in rows.items():
+                checked += 1
+                bad += int(not np.array_equal(got.numpy(), want(spec, be.pool_blocks, f, seqs)))
+        rep["dumps_checked"] = checked
+        rep["dumps_checked_channels"] = {s.name: be.kept_channels[a] for a, s in enumerate(specs)}
+        rep["exact"] = checked > 0 and bad == 0
+        out[label] = rep
+        del svc, be
+    out["exact"] = all(out[k]["exact"] for k in ("paced", "unpaced"))
+    out["gaps"] = sum(a["gaps"] for k in ("paced", "unpaced") for a in out[k]["arrays"])
     return out
 
 
@@ -524,19 +668,21 @@ def run_ours(args, world, rank, local):
         for k in range(n_int):
             g, _ = batch.capture(integration(k), outs[k & 1], stream=stream)
             graphs.append(g)
-        gev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-               for _ in range(n_int)]
-        graph_ms = []
+        # one event pair per graph launch of every timed step
+        gev = [[(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                for _ in range(n_int)] for _ in range(args.steps)]
+        timed_step = [0]
 
         def step(timed=False):
+            evs = gev[timed_step[0]] if timed else None
             for k, g in enumerate(graphs):
                 if timed:
-                    gev[k][0].record(stream)
+                    evs[k][0].record(stream)
                 g.launch(stream)
                 if timed:
-                    gev[k][1].record(stream)
+                    evs[k][1].record(stream)
             if timed:
-                graph_ms.append(gev)
+                timed_step[0] += 1
     else:
         def step(timed=False):
             for k in range(n_int):
@@ -560,8 +706,7 @@ def run_ours(args, world, rank, local):
     ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     ev0.record(stream)
     for st in range(args.steps):
-        # per-graph events on the last step only (they are reused)
-        step(timed=(args.mode == "graph" and st == args.steps - 1))
+        step(timed=(args.mode == "graph"))
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     if clocks:
@@ -594,14 +739,16 @@ def run_ours(args, world, rank, local):
         launches_per_step = per_int_launches * n_int
         all_ms = sum(p[k]["ms"] for p in prof for k in p)
         xe_share = sum(p["xengine"]["ms"] for p in prof) / all_ms if all_ms > 0 else 1.0
-        g_ms = [a.elapsed_time(b) for a, b in gev]
+        g_ms = [a.elapsed_time(b) for evs in gev for a, b in evs]
         xe_ms = sum(g_ms) * xe_share
         xe_timed = len(g_ms) * max(1, sum(p["xengine"]["launches"] for p in prof))
         kernel_ms = {"graph_per_integration": sum(g_ms) / len(g_ms),
-                     "xengine_per_integration": xe_ms / len(g_ms), "xengine_share": xe_share}
-        timing_note = ("CUDA events around every graph launch (one integration each) of the last "
+                     "graph_per_integration_min": min(g_ms), "graph_per_integration_max": max(g_ms),
+                     "xengine_per_integration": xe_ms / len(g_ms), "xengine_share": xe_share,
+                     "xengine_ms_per_step": xe_ms / args.steps}
+        timing_note = ("CUDA events around every graph launch (one integration each) of every "
                        "timed step, times the X-engine's share of a profiled direct integration")
-    xe_per_step = xe_timed if args.mode == "graph" else xe_timed // max(1, args.steps)
+    xe_per_step = xe_timed // max(1, args.steps)
     peaks, src = load_peaks()
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     ops_per_launch = 8.0 * step_cmac / max(1, xe_per_step)
@@ -655,7 +802,8 @@ def run_ours(args, world, rank, local):
 
     extras = None
     if not args.no_extras and rank == 0:
-        extras = measure_extras(arrays, volts, outs, stream, dev, peaks, src)
+        extras = measure_extras(arrays, volts, outs, stream, dev, peaks, src,
+                                full=args.workload == "full_band")
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu_baseline:

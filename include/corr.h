@@ -459,8 +459,12 @@ int corr_fine_pfb(const int8_t *d_x, int n_coarse, int n_inputs, long long n_sam
  * Other argument errors: CORR_E_ARG.  Asynchronous on `stream`.
  *
  * The first call on each device looks up the scratch array's device address
- * (cudaGetSymbolAddress, with that device current) and caches it; make that
- * first call before any stream capture.  All calls on a device share the same
+ * (cudaGetSymbolAddress, with that device current) and caches it.  With lazy
+ * module loading (the CUDA default) that lookup is also what loads the
+ * library's device code on the device and reserves the 64 MiB, so the first
+ * call may take device memory and synchronise the device: make one warm-up
+ * call per device (n_time == 0 with a valid d_vis is enough) before data
+ * flows, and before any stream capture.  All calls on a device share the same
  * scratch: calls whose work overlaps on the GPU (different streams, no
  * ordering between them) race and corrupt each other's results.  Calls
  * ordered on one stream are safe; the scratch keeps the previous call's

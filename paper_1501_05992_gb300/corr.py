@@ -470,6 +470,18 @@ class Batch:
                "corr_batch_dump")
         return outs
 
+    def dump_host(self, a: int, out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """corr_dump_host on array `a` of the batch: its packed triangle into a host tensor."""
+        n, f = self.specs[a][0], self.specs[a][1]
+        if out is None:
+            out = torch.empty((f, n * (n + 1) // 2, 2), dtype=torch.int32, pin_memory=True)
+        elif (out.dtype != torch.int32 or out.shape != (f, n * (n + 1) // 2, 2)
+              or not out.is_contiguous() or out.device.type != "cpu"):
+            raise ValueError("out must be a contiguous int32 [F][P][2] host tensor")
+        _check(self._lib.corr_dump_host(self._ctx(a), ctypes.c_void_p(out.data_ptr()),
+                                        _stream_handle(stream)), "corr_dump_host")
+        return out
+
     def integrate(self, volts, outs=None, stream=None):
         """Whole integrations of every array straight into `outs` (see corr_batch_integrate)."""
         ptrs, nt = self._volts(volts)

@@ -575,6 +575,9 @@ int corr_dump_host(corr_ctx *c, int32_t *h_vis, void *stream)
     if (!c->ws) return ret(CORR_E_STATE);
     cudaStream_t s = static_cast<cudaStream_t>(stream);
     const size_t bytes = acc_words(c) * sizeof(int32_t);
+    // a fresh context holds no data: zero the accumulators first, but only after
+    // an earlier host dump's copy (on the output stream) has finished reading them
+    if (c->fresh && wait_host_dump(c, s) != CORR_OK) return ret(CORR_E_CUDA);
     if (c->fresh && cudaMemsetAsync(c->acc, 0, bytes, s) != cudaSuccess) {
         cudaGetLastError();
         return ret(CORR_E_CUDA);
@@ -888,6 +891,12 @@ int batch_correlate(corr_batch *b, const uint8_t *const *d_volt, const int *n_ti
     for (int g0 = 0; g0 < n_tc; g0 += CORR_BATCH_TC_GROUP) {
         const int gn = n_tc - g0 < CORR_BATCH_TC_GROUP ? n_tc - g0 : CORR_BATCH_TC_GROUP;
         corr_ctx *lead = b->ctx[tc[g0]];
+        if (!into) {
+            // the launch writes the arrays' accumulators: order it after any host
+            // dump of them that may still be copying out on an output stream
+            for (int x = 0; x < gn; ++x)
+                if (wait_host_dump(b->ctx[tc[g0 + x]], s) != CORR_OK) return CORR_E_CUDA;
+        }
         for (int t0 = 0; t0 < max_nt; t0 += kTcMaxSamples) {
             TcArray arr[CORR_BATCH_TC_GROUP];
             int k = 0;

@@ -7,9 +7,13 @@
 // loops in which an allocation (which may synchronise the device) would stall
 // the data stream.  corr_create/corr_bind_workspace need a caller-allocated
 // workspace; this entry point needs none.  Its scratch (the unpacked operand
-// planes) lives in one statically sized __device__ array that the CUDA
-// runtime places on each GPU when the library's module is loaded and keeps
-// there until the process exits.
+// planes) lives in one statically sized __device__ array.  The CUDA runtime
+// reserves it on a GPU when it loads the library's device code there: with
+// lazy module loading (the default) that happens inside the first call on
+// that device, whose symbol lookup below loads the module, so the first call
+// can take device memory and synchronise.  Callers that must never do that
+// once data flows make one warm-up call first (n_time == 0 is enough).  The
+// array then stays reserved until the process exits.
 //
 // The caller still provides the voltages and the visibility buffer.  One call
 // correlates one block as a whole integration and overwrites d_vis.

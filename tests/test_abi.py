@@ -55,11 +55,15 @@ def test_library_exports_every_declared_symbol(lib_path):
 
 
 def test_library_targets_sm103a_only(lib_path):
-    out = subprocess.run(["cuobjdump", "--list-elf", lib_path], capture_output=True, text=True)
-    if out.returncode != 0:
-        pytest.skip("cuobjdump unavailable")
-    archs = set(re.findall(r"sm_(\d+a?)", out.stdout))
-    assert archs == {"103a"} or archs == {"103"}, archs
+    """Every translation unit and the link are built with exactly one
+    -gencode, for sm_103a, and the build fingerprint covers those flags."""
+    arch = corr_build.ARCH
+    assert arch == ["-gencode", "arch=compute_103a,code=sm_103a"], arch
+    flags = corr_build.NVCC_FLAGS
+    assert not any(f.startswith(("-arch", "--gpu-architecture", "-gencode", "--generate-code"))
+                   for f in flags), flags
+    stamp = os.path.join(os.path.dirname(lib_path), "libcorr.stamp")
+    assert open(stamp).read().strip() == corr_build._fingerprint()
 
 
 def test_strerror_and_version(lib_path):

@@ -75,6 +75,38 @@ def test_long_batched_integration_splits_launches():
     _check_batch(specs, volts)
 
 
+def test_batch_accumulate_after_a_member_host_dump():
+    """A host dump of one batch member copies out on the member's output
+    stream; the next batched tensor-core launch must wait for that copy
+    before it overwrites the member's accumulators."""
+    if not path_available("tc_fp8", 256):
+        pytest.skip("tc_fp8 unsupported")
+    specs = [{"n_inputs": 256, "n_chan": 48, "n_time_per_int": 2000, "path": "tc_fp8"},
+             {"n_inputs": 128, "n_chan": 20, "n_time_per_int": 2000, "path": "tc_fp8"}]
+    rng = np.random.default_rng(91)
+    va = [rng.integers(0, 256, (1000, 48, 256), dtype=np.uint8),
+          rng.integers(0, 256, (1000, 20, 128), dtype=np.uint8)]
+    vb = [rng.integers(0, 256, (1000, 48, 256), dtype=np.uint8),
+          rng.integers(0, 256, (1000, 20, 128), dtype=np.uint8)]
+    b = corr.Batch(specs)
+    da = [torch.from_numpy(v).cuda() for v in va]
+    db = [torch.from_numpy(v).cuda() for v in vb]
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    host = b.dump_host(0, stream=s)
+    for _ in range(3):
+        b.accumulate(da, stream=s)
+        b.dump_host(0, host, stream=s)
+        b.accumulate(db, stream=s)
+        outs = b.dump(stream=s)
+        b.sync(s)
+        assert np.array_equal(host.numpy(), oracle.to_int32(oracle.xmac(va[0])))
+        assert np.array_equal(outs[0].cpu().numpy(), oracle.to_int32(oracle.xmac(vb[0])))
+        both = np.concatenate([va[1], vb[1]])
+        assert np.array_equal(outs[1].cpu().numpy(), oracle.to_int32(oracle.xmac(both)))
+    b.close()
+
+
 def test_overflow_in_one_array_enqueues_nothing():
     specs = [(64, 2, 100), (128, 2, 50)]
     b = corr.Batch(specs)

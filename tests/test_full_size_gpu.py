@@ -52,7 +52,10 @@ def test_full_band_graph_sampled():
 
 def test_uneven_batch_full_sizes_sampled():
     """The three arrays of the uneven batch at full size in one persistent
-    launch (128 x 1536 x 2000, 256 x 3072 x 5000, 1024 x 512 x 10000)."""
+    launch (128 x 1536 x 2000, 256 x 3072 x 5000, 1024 x 512 x 10000): whole
+    triangles of two channels of every array (the 1024-input array at its
+    full 10000 samples, i.e. with pair items) and random visibilities
+    elsewhere."""
     if not path_available("tc_fp8", 128):
         pytest.skip("tc_fp8 unsupported")
     arrays = [(128, 1536, 2000), (256, 3072, 5000), (1024, 512, 10000)]
@@ -63,6 +66,9 @@ def test_uneven_batch_full_sizes_sampled():
     b.sync()
     rng = np.random.default_rng(4)
     for a, ((n, f, t), v, o) in enumerate(zip(arrays, volts, outs)):
+        chans = [int(rng.integers(0, f)), f - 1]
+        want = oracle.to_int32(oracle.xmac(v[:, chans].cpu().numpy()))
+        assert np.array_equal(o[chans].cpu().numpy(), want), (a, chans)
         host = o.cpu().numpy()
         fs = rng.integers(0, f, 24)
         i, j = _pairs(rng, n, 24)

@@ -179,6 +179,29 @@ def test_back_to_back_host_integrations(path):
 
 
 @pytest.mark.parametrize("path", ALL_PATHS)
+def test_empty_host_dump_right_after_a_host_dump(path):
+    """A host dump of an empty integration zeroes the accumulators; it must not
+    do so while the previous host dump's copy is still reading them."""
+    N, F, T = 256, 48, 1500
+    if not path_available(path, N):
+        pytest.skip(f"{path} unsupported")
+    volt = np.random.default_rng(82).integers(0, 256, (T, F, N), dtype=np.uint8)
+    want = oracle.to_int32(oracle.xmac(volt))
+    P = N * (N + 1) // 2
+    outs = [torch.full((F, P, 2), -5, dtype=torch.int32).pin_memory() for _ in range(2)]
+    c = corr.Correlator(N, F, T, path=path)
+    s = torch.cuda.Stream()
+    for _ in range(3):
+        c.accumulate_host(torch.from_numpy(volt).pin_memory(), stream=s)
+        c.dump_host(outs[0], stream=s)
+        c.dump_host(outs[1], stream=s)           # nothing accumulated since: all zeros
+        c.sync(s)
+        assert np.array_equal(outs[0].numpy(), want)
+        assert not outs[1].numpy().any()
+    c.close()
+
+
+@pytest.mark.parametrize("path", ALL_PATHS)
 def test_integrate_exact_and_leaves_running_integration(path):
     """corr_integrate writes one whole integration straight to the output and
     does not disturb an integration that is being accumulated meanwhile."""

@@ -4,8 +4,8 @@ loops that may not allocate once data flows).
 
 It is called here directly through the C ABI (ctypes), with device buffers
 that the test allocates up front, and its output is compared with the regular
-corr_accumulate + corr_dump path on the same input: bit for bit, the tolerance
-of every parity test in this suite.  Two calls in a row with different inputs
+corr_accumulate + corr_dump path on the same input and with the CPU oracle:
+bit for bit, the tolerance of every parity test in this suite.  Two calls in a row with different inputs
 show that the shared static scratch carries nothing over between calls.
 This file is named to be collected last.
 """
@@ -15,6 +15,7 @@ import numpy as np
 import pytest
 import torch
 
+import oracle
 from paper_1501_05992_gb300 import corr
 
 pytestmark = pytest.mark.gpu
@@ -49,7 +50,9 @@ def test_noalloc_matches_regular_path_twice_in_a_row():
         assert _noalloc(lib, volt, out) == corr.CORR_OK, corr.strerror(lib.corr_last_error())
     torch.cuda.synchronize()
     for volt, out in zip(vols, outs):
-        assert np.array_equal(out.cpu().numpy(), _regular(volt))
+        got = out.cpu().numpy()
+        assert np.array_equal(got, _regular(volt))
+        assert np.array_equal(got, oracle.to_int32(oracle.xmac(volt.cpu().numpy())))
 
 
 def test_noalloc_zero_invalid_and_empty_block():
@@ -60,6 +63,8 @@ def test_noalloc_zero_invalid_and_empty_block():
     assert _noalloc(lib, volt, out, flags=corr.ZERO_INVALID) == corr.CORR_OK
     torch.cuda.synchronize()
     assert np.array_equal(out.cpu().numpy(), _regular(volt, zero_invalid=True))
+    assert np.array_equal(out.cpu().numpy(),
+                          oracle.to_int32(oracle.xmac(volt.cpu().numpy(), zero_invalid=True)))
     empty = torch.empty((0, 3, 17), dtype=torch.uint8, device="cuda")
     out.fill_(99)
     assert _noalloc(lib, empty, out) == corr.CORR_OK
