@@ -758,7 +758,11 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             if (!pair) next_slot ^= 1;
             const int sbuf = local & 1;
             int *sb = sums + sbuf * (2 * 2 * kTile);
-            const int *sj = sb + 1 * 2 * kTile;                   // J tile sums: [r/m][slot]
+            int *sj = sb + 1 * 2 * kTile;                          // J tile sums: [r/m][slot]
+            // this thread's input in the I and J tiles: its row terms (E, D of Section
+            // 5's offset corrections), read before the J sums become column terms
+            int EiI = 0, DiI = 0, EiJ = 0, DiJ = 0;
+            const int il = q * 32 + lane;
             const int n_parts = pair ? 2 : 1;
             for (int part = 0; part < n_parts; ++part) {
                 const int sl = part == 0 ? s0 : s1;
@@ -775,16 +779,32 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 if (lane == 0) epi_ok[q] = mine ? 1 : 0;
                 named_sync(2, kEpiWarps * 32);
                 ok = epi_ok[0] && epi_ok[1] && epi_ok[2] && epi_ok[3];
+                if (ok && part == 0) {
+                    const int SrJ = sj[sum_slot(il)], SmJ = sj[kTile + sum_slot(il)];
+                    const int SrI = sb[sum_slot(il)], SmI = sb[kTile + sum_slot(il)];
+                    EiJ = SrJ + SmJ;
+                    DiJ = SmJ - SrJ;
+                    EiI = SrI + SmI;
+                    DiI = SmI - SrI;
+                    named_sync(2, kEpiWarps * 32);
+                    // column j's terms of the corrections, as floats in column order
+                    // (the J sums area holds exactly 128 float2): -8 E_j for Re, 8 D_j for Im
+                    reinterpret_cast<float2 *>(sj)[il] = make_float2(float(-8 * EiJ), float(8 * DiJ));
+                }
                 named_sync(2, kEpiWarps * 32);
                 if (!ok) break;
                 slot_phase ^= 1u << sl;
                 fence_after();
-                const int *si = sb + (diag ? 1 : 0) * 2 * kTile;     // I tile sums
-                const int il = q * 32 + lane;
                 const int i = I * kTile + il;
-                const int Sri = si[sum_slot(il)], Smi = si[kTile + sum_slot(il)];
-                const int Ei = Sri + Smi, Di = Smi - Sri;
-                const int base_re = 128 * T_eff - 8 * Ei;
+                const int Ei = diag ? EiJ : EiI, Di = diag ? DiJ : DiI;
+                // Re V = P_re - 8 E_j + (128 T - 8 E_i) and Im V = P_im + 8 D_j - 8 D_i,
+                // computed in fp32 on integer values: P = TMEM * 2^18 and every partial
+                // sum is an integer below 2^24 in magnitude, so each step is exact, and
+                // adding 1.5 * 2^23 leaves V (|V| <= 128 T <= 2^22) as the low bits of
+                // the float's encoding
+                const float row_re = float(128 * T_eff - 8 * Ei) + 12582912.0f;
+                const float row_im = float(-8 * Di) + 12582912.0f;
+                const float4 *col = reinterpret_cast<const float4 *>(sj);
                 int32_t *out = acc + ((size_t)f * P + (size_t)i * (i + 1) / 2) * 2;
                 const uint32_t taddr = tmem + uint32_t(sl * 256) + (uint32_t(q * 32) << 16);
 #pragma unroll 1
@@ -795,30 +815,45 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                     tmem_wait_ld();
                     // columns c0 .. c0 + 7 of row i that lie in the lower triangle
                     const int kmax = i < n_in ? min(7, i - (J * kTile + c0)) : -1;
-                    if (kmax >= 0) {
-                        int2 *dst = reinterpret_cast<int2 *>(out) + (J * kTile + c0);
-                        int2 prev[8];
-                        if (!fresh) {
-                            // issue every load of the chunk before the first store
+                    if (kmax < 0) continue;
+                    int2 *dst = reinterpret_cast<int2 *>(out) + (J * kTile + c0);
+                    int2 v[8];
+                    if (!fresh) {
+                        // issue every load of the chunk before the first store
 #pragma unroll
-                            for (int k = 0; k < 8; ++k)
-                                prev[k] = k <= kmax ? dst[k] : make_int2(0, 0);
-                        }
+                        for (int k = 0; k < 8; ++k) v[k] = k <= kmax ? dst[k] : make_int2(0, 0);
+                    } else {
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            if (k > kmax) continue;
-                            const int jl = c0 + k;
-                            const int Srj = sj[sum_slot(jl)], Smj = sj[kTile + sum_slot(jl)];
-                            const int pre = __float2int_rn(__uint_as_float(vre[k]) * 262144.0f);
-                            const int pim = __float2int_rn(__uint_as_float(vim[k]) * 262144.0f);
-                            int re = pre + base_re - 8 * (Srj + Smj);
-                            int im = pim - 8 * Di + 8 * (Smj - Srj);
-                            if (!fresh) {
-                                re += prev[k].x;
-                                im += prev[k].y;
-                            }
-                            dst[k] = make_int2(re, im);
+                        for (int k = 0; k < 8; ++k) v[k] = make_int2(0, 0);
+                    }
+#pragma unroll
+                    for (int k = 0; k < 8; k += 2) {
+                        const float4 c = col[(c0 + k) >> 1];
+                        v[k].x += __float_as_int(fmaf(__uint_as_float(vre[k]), 262144.0f, c.x) + row_re) - 0x4B400000;
+                        v[k].y += __float_as_int(fmaf(__uint_as_float(vim[k]), 262144.0f, c.y) + row_im) - 0x4B400000;
+                        v[k + 1].x +=
+                            __float_as_int(fmaf(__uint_as_float(vre[k + 1]), 262144.0f, c.z) + row_re) - 0x4B400000;
+                        v[k + 1].y +=
+                            __float_as_int(fmaf(__uint_as_float(vim[k + 1]), 262144.0f, c.w) + row_im) - 0x4B400000;
+                    }
+                    if (kmax == 7) {
+                        // 16-byte stores where the row allows (a packed row starts on any
+                        // 8-byte element): half the store instructions, half the sectors
+                        if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+                            for (int k = 0; k < 8; k += 2)
+                                *reinterpret_cast<int4 *>(dst + k) = make_int4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
+                        } else {
+                            dst[0] = v[0];
+#pragma unroll
+                            for (int k = 1; k < 7; k += 2)
+                                *reinterpret_cast<int4 *>(dst + k) = make_int4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
+                            dst[7] = v[7];
                         }
+                    } else {
+#pragma unroll
+                        for (int k = 0; k < 8; ++k)
+                            if (k <= kmax) dst[k] = v[k];
                     }
                 }
                 // this part's TMEM slot can take the next accumulation
