@@ -24,18 +24,23 @@
 // samples (samples past the end of the block are zero bytes, i.e. u = 8, and
 // cancel exactly).
 //
-// Complex -> real: with planes R (ur), M (um), nM (-um) of the J tile, two
-// MMAs per 32 samples, each M=128 x N=256 x K=32, fill D = [Re | Im]:
-//   D += R_I . [R_J ; nM_J]^T   ->  [ sum ur ur | -sum ur um ]
-//   D += M_I . [M_J ; R_J ]^T   ->  [ sum um um |  sum um ur ]
-// Operands are MN-major (inputs contiguous, the natural [t][n] order of the
-// voltages), 128-byte swizzled, so no transpose is ever needed.
+// Complex -> real: for the tile pair (I, J), I >= J, the MMA's A operand (the
+// 128 TMEM lanes) is the J tile and its B operand (the TMEM columns) the I
+// tile.  With planes R (ur), M (um), nM (-um), two MMAs per 32 samples, each
+// M=128 x N=256 x K=32, fill D = [Re | Im]:
+//   D += R_J . [R_I ; nM_I]^T   ->  [ sum ur_j ur_i | -sum ur_j um_i ]
+//   D += M_J . [M_I ; R_I ]^T   ->  [ sum um_j um_i |  sum um_j ur_i ]
+// i.e. D[a][b] = sum x_a conj(x_b) for input a of J and b of I, and V_ij =
+// conj(D[a][b]).  Operands are MN-major (inputs contiguous, the natural
+// [t][n] order of the voltages), 128-byte swizzled, so no transpose is ever
+// needed.  Lanes on the J side make the epilogue's stores coalesced: a TMEM
+// column read gives 32 lanes = 32 consecutive elements of one packed row.
 //
-// Work items: per channel, a diagonal tile (J, J) and the tile below it
-// (J + 1, J) form one "pair" item, since both multiply by the J tile's planes:
-// the pair converts the two tiles once and issues both MMA chains, into the
-// two TMEM accumulators.  The other tiles (I >= J + 2) are single items, and
-// the last J tile's diagonal is a single item too (for 256 inputs: one pair
+// Work items: per channel, a diagonal tile (I, I) and the tile left of it
+// (I, I - 1) form one "pair" item, since both multiply by the I tile's planes
+// as B: the pair converts the two tiles once and issues both MMA chains, into
+// the two TMEM accumulators.  The other tiles (J <= I - 2) are single items,
+// and the first diagonal (0, 0) is a single item too (for 256 inputs: one pair
 // and one diagonal item per channel, where single items would make three).
 // Launches shorter than kPairMinStages stages use single items only.
 //
@@ -50,6 +55,8 @@
 //              cost); warp 17 is left idle so that the MMA warp's scheduler
 //              (warps 1, 5, 9, ... share one) serves one converter warp fewer
 //   warps 18-21 epilogue: TMEM -> int32, corrections, packed-triangle store
+//              (fp32 on exact integers; each store instruction writes 32
+//              consecutive elements of one packed row)
 // TMEM holds two accumulators (2 x 256 columns).  A single item takes the
 // next one in turn, so its epilogue overlaps the main loop of the next item; a
 // pair item takes both, its diagonal part in the one that is released first.
@@ -75,9 +82,11 @@ constexpr int kPlaneStages = 3;
 constexpr int kPlaneBytes = kTc * 128;        // one E4M3 plane: 64 rows x 128 B = 8 KB
 constexpr int kPackedTileBytes = kTc * kTile; // 8 KB
 constexpr int kPackedStageBytes = 2 * kPackedTileBytes;
-// plane stage layout: R_I | M_I | M_J | R_J | nM_J
-constexpr int kOffRI = 0, kOffMI = kPlaneBytes, kOffMJ = 2 * kPlaneBytes, kOffRJ = 3 * kPlaneBytes,
-              kOffNMJ = 4 * kPlaneBytes;
+// plane stage layout: R_A | M_A | M_B | R_B | nM_B (A: the tile of the TMEM
+// rows, the output's column inputs; B: the tile of the TMEM columns, the
+// output's row inputs)
+constexpr int kOffRA = 0, kOffMA = kPlaneBytes, kOffMB = 2 * kPlaneBytes, kOffRB = 3 * kPlaneBytes,
+              kOffNMB = 4 * kPlaneBytes;
 constexpr int kPlaneStageBytes = 5 * kPlaneBytes;  // 40 KB
 constexpr int kConvWarps = 16, kEpiWarps = 4;
 constexpr int kTeams = 2, kTeamWarps = kConvWarps / kTeams;   // converter teams own alternate stages
@@ -318,11 +327,12 @@ __device__ __forceinline__ void named_sync(int id, int threads)
     asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(threads) : "memory");
 }
 
-// Work items of one channel, for n_tiles tiles of 128 inputs: for each J tile,
-// a pair item covering the tile pairs (J, J) and (J + 1, J) (they share the J
-// tile's planes, so one conversion feeds both, into two accumulators), then
-// the off-diagonal items (I, J) for I >= J + 2; the last J tile has only its
-// diagonal item.  n_tiles (n_tiles + 1) / 2 - (n_tiles - 1) items per channel.
+// Work items of one channel, for n_tiles tiles of 128 inputs (tile pair (I, J)
+// with I >= J: output rows in tile I, columns in tile J): the diagonal item
+// (0, 0), then for each I >= 1 a pair item covering (I, I) and (I, I - 1) (both
+// multiply by the I tile's planes as the B operand, so one conversion feeds
+// both, into two accumulators) and the off-diagonal items (I, J) for
+// J <= I - 2.  n_tiles (n_tiles + 1) / 2 - (n_tiles - 1) items per channel.
 enum ItemKind { kDiagItem = 0, kOffItem = 1, kPairItem = 2 };
 
 __host__ __device__ __forceinline__ int items_per_channel(int n_tiles, bool pairs)
@@ -342,23 +352,25 @@ __device__ __forceinline__ void item_tiles(int k, int n_tiles, bool pairs, int &
         kind = I == J ? kDiagItem : kOffItem;
         return;
     }
-    for (J = 0; J < n_tiles; ++J) {
-        const int cnt = J + 1 < n_tiles ? n_tiles - J - 1 : 1;
-        if (k < cnt) break;
-        k -= cnt;
-    }
-    if (J + 1 < n_tiles) {
-        I = J + 1 + k;
-        kind = k == 0 ? kPairItem : kOffItem;
-    } else {
-        I = J;
+    if (k == 0) {
+        I = J = 0;
         kind = kDiagItem;
+        return;
+    }
+    --k;
+    for (I = 1; I + 1 < n_tiles && k >= I; ++I) k -= I;   // row I holds I items
+    if (k == 0) {
+        J = I - 1;
+        kind = kPairItem;
+    } else {
+        J = k - 1;
+        kind = kOffItem;
     }
 }
 
 struct Item {
     int a, f, I, J, kind;
-    bool diag;      // the producer and the converters see a pair item as the off-diagonal (J + 1, J)
+    bool diag;      // the producer and the converters see a pair item as the off-diagonal (I, I - 1)
 };
 
 __device__ __forceinline__ Item decode_item(const Params &p, int item)
@@ -473,13 +485,13 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 const int f = it.f, I = it.I, J = it.J;
                 const bool diag = it.diag;
                 for (int s = 0; s < kPrefetchStages && s < n_stages; ++s) {
-                    tma_prefetch_3d(tmap, J * kTile, f, s * kTc);
-                    if (!diag) tma_prefetch_3d(tmap, I * kTile, f, s * kTc);
+                    tma_prefetch_3d(tmap, I * kTile, f, s * kTc);
+                    if (!diag) tma_prefetch_3d(tmap, J * kTile, f, s * kTc);
                 }
                 for (int s = 0; s < n_stages; ++s) {
                     if (s + kPrefetchStages < n_stages) {
-                        tma_prefetch_3d(tmap, J * kTile, f, (s + kPrefetchStages) * kTc);
-                        if (!diag) tma_prefetch_3d(tmap, I * kTile, f, (s + kPrefetchStages) * kTc);
+                        tma_prefetch_3d(tmap, I * kTile, f, (s + kPrefetchStages) * kTc);
+                        if (!diag) tma_prefetch_3d(tmap, J * kTile, f, (s + kPrefetchStages) * kTc);
                     }
                     if (!mbar_wait(bar_packed_empty(stage), phase ^ 1u, abort, p.status, 1, p.wait_limit)) {
                         ok = false;
@@ -488,8 +500,9 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                     const uint32_t full = bar_packed_full(stage);
                     const uint32_t dst = sbase + kSmPacked + stage * kPackedStageBytes;
                     mbar_expect_tx(full, diag ? kPackedTileBytes : 2 * kPackedTileBytes);
-                    tma_load_3d(dst + kPackedTileBytes, tmap, full, J * kTile, f, s * kTc);
-                    if (!diag) tma_load_3d(dst, tmap, full, I * kTile, f, s * kTc);
+                    // upper half: the B tile (I); lower half: the A tile (J)
+                    tma_load_3d(dst + kPackedTileBytes, tmap, full, I * kTile, f, s * kTc);
+                    if (!diag) tma_load_3d(dst, tmap, full, J * kTile, f, s * kTc);
                     issued |= 1u << stage;
                     issued_phase = (issued_phase & ~(1u << stage)) | (phase << stage);
                     if (++stage == kPackedStages) {
@@ -537,12 +550,12 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 // address >> 4, below 2^14 for any shared address): build the
                 // plane-stage-0 descriptors once and add offsets.  Part 0 of a pair
                 // (and a diagonal item) multiplies the J planes by themselves.
-                const bool a_is_j = it.kind != kOffItem;
+                const bool a_is_b = it.kind != kOffItem;
                 const uint32_t t0 = tmem + uint32_t(s0 * 256), t1 = tmem + uint32_t(s1 * 256);
-                const uint64_t dR0 = desc_planes + uint64_t((a_is_j ? kOffRJ : kOffRI) >> 4);
-                const uint64_t dM0 = desc_planes + uint64_t((a_is_j ? kOffMJ : kOffMI) >> 4);
-                const uint64_t dR1 = desc_planes + uint64_t(kOffRI >> 4), dM1 = desc_planes + uint64_t(kOffMI >> 4);
-                const uint64_t dRJ = desc_planes + uint64_t(kOffRJ >> 4), dMJ = desc_planes + uint64_t(kOffMJ >> 4);
+                const uint64_t dR0 = desc_planes + uint64_t((a_is_b ? kOffRB : kOffRA) >> 4);
+                const uint64_t dM0 = desc_planes + uint64_t((a_is_b ? kOffMB : kOffMA) >> 4);
+                const uint64_t dR1 = desc_planes + uint64_t(kOffRA >> 4), dM1 = desc_planes + uint64_t(kOffMA >> 4);
+                const uint64_t dRJ = desc_planes + uint64_t(kOffRB >> 4), dMJ = desc_planes + uint64_t(kOffMB >> 4);
                 uint32_t accum = 0;
                 if (pair) {
                     for (int s = 0; s < n_stages; ++s) {
@@ -604,8 +617,11 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
         // barrier latency once per two stages.  Thread u of a team owns chunk
         // column c (16 inputs) of one tile and a set of rows of each of its
         // stages, so its per-input sums cover 16 inputs and stay in registers:
-        //   off-diagonal item: q < 16 -> J tile, q >= 16 -> I tile, rows (q & 15) + 16k, k < 4
-        //   diagonal item:     J tile, rows q + 32k, k < 2
+        //   off-diagonal item: q < 16 -> B tile, q >= 16 -> A tile, rows (q & 15) + 16k, k < 4
+        //   diagonal item:     B tile, rows q + 32k, k < 2
+        // The B tile (upper half of the packed stage) becomes the planes M, R and
+        // -M, the A tile (lower half) R and M; a diagonal item's single tile is
+        // both, as B.
         const int ci = warp <= 16 ? warp - 2 : 15;
         const int team = ci / kTeamWarps;
         const int u = (ci % kTeamWarps) * 32 + lane;   // 0..255
@@ -617,10 +633,10 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             const Item it = decode_item(p, item);
             const int n_stages = p.a[it.a].n_stages;
             const bool diag = it.diag;
-            const bool tile_j = diag || q < 16;
+            const bool tile_b = diag || q < 16;
             const int n_units = diag ? 2 : 4;
             const int row0 = diag ? q : (q & 15), row_step = diag ? 32 : 16;
-            const uint32_t src_tile = tile_j ? uint32_t(kPackedTileBytes) : 0u;
+            const uint32_t src_tile = tile_b ? uint32_t(kPackedTileBytes) : 0u;
             // per-input code sums of this thread's 16 inputs: byte lanes
             // (<= 16 rows of codes <= 15 between widenings), then 16-bit lanes
             uint32_t b8[2][4], s16lo[2][4], s16hi[2][4];
@@ -654,15 +670,15 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                         b8[0][e] += R[e];
                         b8[1][e] += M[e];
                     }
-                    if (tile_j) {
-                        *reinterpret_cast<uint4 *>(pl + kOffMJ + so) = make_uint4(M[0], M[1], M[2], M[3]);
-                        *reinterpret_cast<uint4 *>(pl + kOffRJ + so) = make_uint4(R[0], R[1], R[2], R[3]);
-                        *reinterpret_cast<uint4 *>(pl + kOffNMJ + so) =
+                    if (tile_b) {
+                        *reinterpret_cast<uint4 *>(pl + kOffMB + so) = make_uint4(M[0], M[1], M[2], M[3]);
+                        *reinterpret_cast<uint4 *>(pl + kOffRB + so) = make_uint4(R[0], R[1], R[2], R[3]);
+                        *reinterpret_cast<uint4 *>(pl + kOffNMB + so) =
                             make_uint4(M[0] | 0x80808080u, M[1] | 0x80808080u, M[2] | 0x80808080u,
                                        M[3] | 0x80808080u);
                     } else {
-                        *reinterpret_cast<uint4 *>(pl + kOffRI + so) = make_uint4(R[0], R[1], R[2], R[3]);
-                        *reinterpret_cast<uint4 *>(pl + kOffMI + so) = make_uint4(M[0], M[1], M[2], M[3]);
+                        *reinterpret_cast<uint4 *>(pl + kOffRA + so) = make_uint4(R[0], R[1], R[2], R[3]);
+                        *reinterpret_cast<uint4 *>(pl + kOffMA + so) = make_uint4(M[0], M[1], M[2], M[3]);
                     }
                 }
                 asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
@@ -711,7 +727,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 break;
             }
             if (lane < 8) {
-                int *sb = sums + buf * (2 * 2 * kTile) + (tile_j ? 1 : 0) * 2 * kTile;
+                int *sb = sums + buf * (2 * 2 * kTile) + (tile_b ? 1 : 0) * 2 * kTile;
 #pragma unroll
                 for (int m = 0; m < 2; ++m) {
                     int *row_sums = sb + m * kTile;
@@ -752,23 +768,27 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             int32_t *const acc = p.a[it.a].acc;
             const long long P = n_pairs(n_in);
             const int T_eff = p.a[it.a].n_stages * kTc;
-            const int f = it.f, J = it.J;
+            const int f = it.f;
             const bool pair = it.kind == kPairItem;
             const int s0 = next_slot, s1 = next_slot ^ 1;
             if (!pair) next_slot ^= 1;
             const int sbuf = local & 1;
-            int *sb = sums + sbuf * (2 * 2 * kTile);
-            int *sj = sb + 1 * 2 * kTile;                          // J tile sums: [r/m][slot]
-            // this thread's input in the I and J tiles: its row terms (E, D of Section
-            // 5's offset corrections), read before the J sums become column terms
-            int EiI = 0, DiI = 0, EiJ = 0, DiJ = 0;
+            int *sb = sums + sbuf * (2 * 2 * kTile);               // A tile sums: [r/m][slot]
+            int *sbB = sb + 1 * 2 * kTile;                         // B tile sums
+            // TMEM lane a of a part holds input a of its A tile (an output column
+            // j), TMEM column b (Re) and 128 + b (Im) input b of the B tile (an
+            // output row i): D[a][b] = sum x_a conj(x_b), so V_ij = conj(D[a][b]).
+            // This thread's input a in either tile gives its row terms (E, D of the
+            // offset corrections), read before the B sums become column terms.
+            int EaA = 0, DaA = 0, EaB = 0, DaB = 0;
             const int il = q * 32 + lane;
+            const size_t out_f = (size_t)f * P;
             const int n_parts = pair ? 2 : 1;
             for (int part = 0; part < n_parts; ++part) {
                 const int sl = part == 0 ? s0 : s1;
-                // part 0 of a pair, or a diagonal item: rows of the J tile
-                const bool diag = part == 0 ? it.kind != kOffItem : false;
-                const int I = diag ? J : it.I;
+                // part 0 of a pair, or a diagonal item: the B tile against itself
+                const bool dpart = part == 0 ? it.kind != kOffItem : false;
+                const int At = dpart ? it.I : it.J;
                 // the four epilogue warps decide together whether to go on, so that
                 // none of them is ever left waiting at a named barrier
                 bool mine = warp_wait(bar_acc_full(sl), (slot_phase >> sl) & 1u, abort, p.status, 7, lane,
@@ -780,80 +800,85 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 named_sync(2, kEpiWarps * 32);
                 ok = epi_ok[0] && epi_ok[1] && epi_ok[2] && epi_ok[3];
                 if (ok && part == 0) {
-                    const int SrJ = sj[sum_slot(il)], SmJ = sj[kTile + sum_slot(il)];
-                    const int SrI = sb[sum_slot(il)], SmI = sb[kTile + sum_slot(il)];
-                    EiJ = SrJ + SmJ;
-                    DiJ = SmJ - SrJ;
-                    EiI = SrI + SmI;
-                    DiI = SmI - SrI;
+                    const int SrB = sbB[sum_slot(il)], SmB = sbB[kTile + sum_slot(il)];
+                    const int SrA = sb[sum_slot(il)], SmA = sb[kTile + sum_slot(il)];
+                    EaB = SrB + SmB;
+                    DaB = SmB - SrB;
+                    EaA = SrA + SmA;
+                    DaA = SmA - SrA;
                     named_sync(2, kEpiWarps * 32);
-                    // column j's terms of the corrections, as floats in column order
-                    // (the J sums area holds exactly 128 float2): -8 E_j for Re, 8 D_j for Im
-                    reinterpret_cast<float2 *>(sj)[il] = make_float2(float(-8 * EiJ), float(8 * DiJ));
+                    // input b's column terms, as floats in column order (the B sums
+                    // area holds exactly 128 float2): -8 E_b for Re, -8 D_b for Im
+                    reinterpret_cast<float2 *>(sbB)[il] = make_float2(float(-8 * EaB), float(-8 * DaB));
                 }
                 named_sync(2, kEpiWarps * 32);
                 if (!ok) break;
                 slot_phase ^= 1u << sl;
                 fence_after();
-                const int i = I * kTile + il;
-                const int Ei = diag ? EiJ : EiI, Di = diag ? DiJ : DiI;
-                // Re V = P_re - 8 E_j + (128 T - 8 E_i) and Im V = P_im + 8 D_j - 8 D_i,
-                // computed in fp32 on integer values: P = TMEM * 2^18 and every partial
-                // sum is an integer below 2^24 in magnitude, so each step is exact, and
-                // adding 1.5 * 2^23 leaves V (|V| <= 128 T <= 2^22) as the low bits of
-                // the float's encoding
-                const float row_re = float(128 * T_eff - 8 * Ei) + 12582912.0f;
-                const float row_im = float(-8 * Di) + 12582912.0f;
-                const float4 *col = reinterpret_cast<const float4 *>(sj);
-                int32_t *out = acc + ((size_t)f * P + (size_t)i * (i + 1) / 2) * 2;
+                const int j = At * kTile + il;                     // this lane's output column
+                const int Ea = dpart ? EaB : EaA, Da = dpart ? DaB : DaA;
+                // Re V_ij = P_re - 8 E_b + (128 T - 8 E_a) and Im V_ij = -P'_im - 8 D_b + 8 D_a,
+                // with P' the TMEM product (Im of x_a conj(x_b)) and b = i, a = j:
+                // computed in fp32 on integer values (TMEM * 2^18 is the integer
+                // product sum, every partial sum is below 2^24 in magnitude, so each
+                // step is exact), and adding 1.5 * 2^23 leaves V (|V| <= 128 T <=
+                // 2^22) as the low bits of the float's encoding
+                const float row_re = float(128 * T_eff - 8 * Ea) + 12582912.0f;
+                const float row_im = float(8 * Da) + 12582912.0f;
+                const float4 *col = reinterpret_cast<const float4 *>(sbB);
                 const uint32_t taddr = tmem + uint32_t(sl * 256) + (uint32_t(q * 32) << 16);
+                const int i0 = it.I * kTile;
+                // in the diagonal part, column b holds output row i0 + b, whose
+                // columns j <= i: chunks wholly left of this warp's lanes are skipped
+                const int c_first = dpart ? ((32 * q) & ~7) : 0;
+                int2 *const colp = reinterpret_cast<int2 *>(acc) + out_f + j;
 #pragma unroll 1
-                for (int c0 = 0; c0 < kTile; c0 += 8) {
+                for (int c0 = c_first; c0 < kTile && i0 + c0 < n_in; c0 += 8) {
                     uint32_t vre[8], vim[8];
                     tmem_ld8(taddr + c0, vre);
                     tmem_ld8(taddr + 128 + c0, vim);
-                    tmem_wait_ld();
-                    // columns c0 .. c0 + 7 of row i that lie in the lower triangle
-                    const int kmax = i < n_in ? min(7, i - (J * kTile + c0)) : -1;
-                    if (kmax < 0) continue;
-                    int2 *dst = reinterpret_cast<int2 *>(out) + (J * kTile + c0);
+                    // element k: output row i = ic + k, column j (this lane):
+                    // consecutive lanes write consecutive elements of the row
+                    const int ic = i0 + c0;
+                    int2 *const p0 = colp + (size_t)(unsigned(ic) * unsigned(ic + 1) / 2u);
+                    const bool full = ic + 7 < n_in && (!dpart || c0 >= 32 * q + 32);
                     int2 v[8];
                     if (!fresh) {
-                        // issue every load of the chunk before the first store
+                        int2 *pk = p0;
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) v[k] = k <= kmax ? dst[k] : make_int2(0, 0);
+                        for (int k = 0; k < 8; ++k) {
+                            const bool use = full || (ic + k < n_in && (!dpart || il <= c0 + k));
+                            v[k] = use ? *pk : make_int2(0, 0);
+                            pk += ic + k + 1;
+                        }
                     } else {
 #pragma unroll
                         for (int k = 0; k < 8; ++k) v[k] = make_int2(0, 0);
                     }
+                    tmem_wait_ld();
 #pragma unroll
                     for (int k = 0; k < 8; k += 2) {
                         const float4 c = col[(c0 + k) >> 1];
                         v[k].x += __float_as_int(fmaf(__uint_as_float(vre[k]), 262144.0f, c.x) + row_re) - 0x4B400000;
-                        v[k].y += __float_as_int(fmaf(__uint_as_float(vim[k]), 262144.0f, c.y) + row_im) - 0x4B400000;
+                        v[k].y += __float_as_int(fmaf(__uint_as_float(vim[k]), -262144.0f, c.y) + row_im) - 0x4B400000;
                         v[k + 1].x +=
                             __float_as_int(fmaf(__uint_as_float(vre[k + 1]), 262144.0f, c.z) + row_re) - 0x4B400000;
                         v[k + 1].y +=
-                            __float_as_int(fmaf(__uint_as_float(vim[k + 1]), 262144.0f, c.w) + row_im) - 0x4B400000;
+                            __float_as_int(fmaf(__uint_as_float(vim[k + 1]), -262144.0f, c.w) + row_im) - 0x4B400000;
                     }
-                    if (kmax == 7) {
-                        // 16-byte stores where the row allows (a packed row starts on any
-                        // 8-byte element): half the store instructions, half the sectors
-                        if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+                    int2 *pk = p0;
+                    if (full) {
 #pragma unroll
-                            for (int k = 0; k < 8; k += 2)
-                                *reinterpret_cast<int4 *>(dst + k) = make_int4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
-                        } else {
-                            dst[0] = v[0];
-#pragma unroll
-                            for (int k = 1; k < 7; k += 2)
-                                *reinterpret_cast<int4 *>(dst + k) = make_int4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
-                            dst[7] = v[7];
+                        for (int k = 0; k < 8; ++k) {
+                            *pk = v[k];
+                            pk += ic + k + 1;
                         }
                     } else {
 #pragma unroll
-                        for (int k = 0; k < 8; ++k)
-                            if (k <= kmax) dst[k] = v[k];
+                        for (int k = 0; k < 8; ++k) {
+                            if (ic + k < n_in && (!dpart || il <= c0 + k)) *pk = v[k];
+                            pk += ic + k + 1;
+                        }
                     }
                 }
                 // this part's TMEM slot can take the next accumulation
