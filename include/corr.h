@@ -98,14 +98,27 @@ corr_ctx *corr_create(int n_inputs, int n_chan, int n_time_per_int);
 /* Release the context (host memory only; the workspace stays the caller's). */
 int corr_destroy(corr_ctx *ctx);
 
-/* Select the implementation.  CORR_E_UNSUPPORTED if the path cannot run this
- * shape on this device (e.g. CORR_PATH_TC_FP8 needs n_inputs % 16 == 0 and a
- * sm_103 device).  Valid only between integrations (corr_samples() == 0),
- * else CORR_E_STATE.  The default is CORR_PATH_AUTO. */
+/* Select the implementation.  CORR_E_UNSUPPORTED if the path cannot run on
+ * this device (CORR_PATH_TC_FP8 needs an sm_103 device).  The tensor-core
+ * path reads the voltage rows through TMA, which needs rows on 16-byte
+ * boundaries: with n_inputs % 16 != 0 each call's samples are first copied
+ * into rows of round_up(n_inputs, 16) bytes in the workspace (up to 256 MiB,
+ * in chunks of a multiple of 64 samples), and in a batch such arrays are
+ * correlated in launches of their own.  AUTO picks the tensor-core path from
+ * 64 inputs on.  Valid only between integrations (corr_samples() == 0), else
+ * CORR_E_STATE.  The default is CORR_PATH_AUTO. */
 int corr_set_path(corr_ctx *ctx, int path);
 
-/* Tile of the CUDA-core path: 32 or 64 inputs per side, or 0 to choose by
- * shape (32 when n_inputs <= 32).  Only between integrations (CORR_E_STATE). */
+/* Tile shape (Section 3.4.2, Eq. 4: the tile sets the arithmetic intensity).
+ * CUDA-core path: 32 or 64 inputs per side.  tcgen05 path: 128 = every work
+ * item one 128 x 128 tile pair (one TMEM accumulator each, so an item's
+ * epilogue overlaps the next item's MMAs); 256 = pair items, a diagonal tile
+ * and the tile left of it as one 256-row column of the triangle (one
+ * conversion of the shared tile feeds two accumulators).  0 chooses by shape:
+ * 32 when n_inputs <= 32 on the CUDA-core path; pair items from 64 stages
+ * of 64 samples per launch on the tcgen05 path.  A value that does not apply
+ * to the context's path is ignored by it.  Any other value: CORR_E_ARG.  Only
+ * between integrations (CORR_E_STATE). */
 int corr_set_tile(corr_ctx *ctx, int tile);
 
 /* The path that accumulate calls will run (AUTO resolved). */
@@ -135,7 +148,9 @@ int corr_bind_workspace(corr_ctx *ctx, void *d_ws, size_t bytes);
  * d_volt is a device pointer to uint8 [n_time][n_chan][n_inputs] (layout
  * above).  n_time == 0 is a no-op.  CORR_E_OVERFLOW (nothing enqueued) if
  * corr_samples() + n_time > n_time_per_int; CORR_E_STATE if no workspace is
- * bound; CORR_E_ARG on NULL d_volt or negative n_time.  Asynchronous.
+ * bound; CORR_E_ARG on NULL d_volt or negative n_time, and on the tensor-core
+ * path with n_inputs % 16 == 0 (read in place by TMA) if d_volt is not
+ * 16-byte aligned.  Asynchronous.
  */
 int corr_accumulate(corr_ctx *ctx, const uint8_t *d_volt, int n_time, void *stream);
 
@@ -248,7 +263,7 @@ typedef struct corr_array_desc {
     int n_time_per_int;  /* samples per integration (cap) */
     int path;            /* CORR_PATH_* for this array; AUTO picks per shape */
     unsigned flags;      /* CORR_ZERO_INVALID or 0 */
-    int tile;            /* CUDA-core tile (corr_set_tile), 0 = by shape */
+    int tile;            /* tile shape (corr_set_tile), 0 = by shape */
 } corr_array_desc;
 
 typedef struct corr_batch corr_batch;

@@ -4,9 +4,13 @@ For an array of N inputs x F channels x T samples per integration, every
 candidate (path, tile) the device supports is timed on a probe block of the
 same N and T (random bytes: the kernels' speed does not depend on the values)
 with a bounded number of channels, and the fastest is kept in a JSON cache
-keyed by device name and shape.  The candidates are the library's tile shapes:
-tcgen05 FP8 on 128 x 128-input tiles, int8 mma.sync on 64 x 64, and the dp4a
-CUDA-core kernel on 64 x 64 or 32 x 32 tiles.
+keyed by device name and shape.  The candidates are the library's tile shapes
+(Section 3.4.2: the tile sets the arithmetic intensity): tcgen05 FP8 with
+every work item one 128 x 128 tile pair (tile 128; each item's epilogue
+overlaps the next item's MMAs) or with pair items, a diagonal tile and the
+tile left of it as one 256-row column sharing one conversion (tile 256);
+int8 mma.sync on 64 x 64; and the dp4a CUDA-core kernel on 64 x 64 or
+32 x 32 tiles.
 """
 from __future__ import annotations
 
@@ -18,7 +22,7 @@ import torch
 
 from . import corr
 
-CANDIDATES = [("tc_fp8", 0), ("mma_i8", 0), ("cudacore", 64), ("cudacore", 32)]
+CANDIDATES = [("tc_fp8", 256), ("tc_fp8", 128), ("mma_i8", 0), ("cudacore", 64), ("cudacore", 32)]
 _lock = threading.Lock()
 
 

@@ -226,7 +226,9 @@ class Correlator:
         return PATH_NAMES[self._lib.corr_get_path(self._ctx)]
 
     def set_tile(self, tile: int) -> None:
-        """CUDA-core tile: 32, 64 or 0 (by shape)."""
+        """Tile shape (corr_set_tile): 32 or 64 for the CUDA-core path, 128
+        (single tile-pair items) or 256 (pair items) for the tcgen05 path,
+        0 to choose by shape."""
         _check(self._lib.corr_set_tile(self._ctx, int(tile)), f"corr_set_tile({tile})")
 
     def set_wait_limit(self, cycles: int) -> None:

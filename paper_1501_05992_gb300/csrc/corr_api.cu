@@ -38,7 +38,7 @@ struct corr_ctx {
     int n = 0, f = 0, t_max = 0;
     int device = 0, sm_major = 0, sm_minor = 0, sm_count = 0;
     int path = CORR_PATH_AUTO;
-    int tile = 0;            // CUDA-core tile (32 or 64), 0 = chosen by shape
+    int tile = 0;            // CUDA-core tile (32 or 64) or tcgen05 items (128, 256); 0 = chosen by shape
     long long wait_limit = 0;   // device bounded-wait limit (cycles), 0 = default
     bool inject_stall = false;  // one-shot test hook for the next tensor-core launch
     unsigned flags = 0;
@@ -50,6 +50,7 @@ struct corr_ctx {
     int32_t *acc = nullptr;
     uint8_t *stage = nullptr;
     uint8_t *host_stage[kHostBuffers] = {};
+    uint8_t *tc_pad = nullptr;   // 16-byte-aligned rows for the tensor-core path (n % 16 != 0)
 
     StagePlan dp4a{}, mma{};
     int host_chunk = 0;
@@ -84,8 +85,21 @@ int ret(int status)
 }
 
 struct WsLayout {
-    size_t status_off, acc_off, stage_off, host_off[kHostBuffers], total;
+    size_t status_off, acc_off, stage_off, host_off[kHostBuffers], pad_off, total;
 };
+
+// Row stride of the tensor-core path's padded copy, and the samples one copy
+// holds (0 when the rows need no padding).
+int tc_ld(int n) { return int(round_up(size_t(n), 16)); }
+int tc_pad_samples(int n, int n_chan, int t_max)
+{
+    if (n % 16 == 0) return 0;
+    const size_t row = size_t(tc_ld(n)) * size_t(n_chan);
+    size_t t = kTcPadCap / row / 64 * 64;
+    if (t < 64) t = 64;
+    const size_t whole = round_up(size_t(t_max), 64);
+    return int(t < whole ? t : whole);
+}
 
 size_t acc_words(const corr_ctx *c) { return size_t(c->f) * size_t(n_pairs(c->n)) * 2; }
 
@@ -105,6 +119,9 @@ WsLayout layout_of(const corr_ctx *c)
         L.host_off[b] = off;
         off = round_up(off + host, kAlign);
     }
+    L.pad_off = off;
+    off = round_up(off + size_t(tc_pad_samples(c->n, c->f, c->t_max)) * size_t(tc_ld(c->n)) * size_t(c->f),
+                   kAlign);
     L.total = off;
     return L;
 }
@@ -163,6 +180,12 @@ void prof_end(corr_ctx *c, int kind, cudaStream_t s, int launches)
     c->prof_cur = {nullptr, nullptr};
 }
 
+// Work-item shape of the tensor-core path chosen by corr_set_tile.
+TcItems tc_items(const corr_ctx *c)
+{
+    return c->tile == 128 ? TcItems::kSingle : c->tile == 256 ? TcItems::kPairs : TcItems::kAuto;
+}
+
 // Order `s` after a host dump that may still be reading the accumulators.
 int wait_host_dump(corr_ctx *c, cudaStream_t s)
 {
@@ -185,15 +208,29 @@ int accumulate_to(corr_ctx *c, const uint8_t *volt, int nt, int32_t *target, boo
     cudaError_t e = cudaSuccess;
     const size_t row = size_t(c->f) * size_t(c->n);
     if (path == CORR_PATH_TC_FP8) {
-        for (int t0 = 0; t0 < nt; t0 += kTcMaxSamples) {
-            const int ntc = nt - t0 < kTcMaxSamples ? nt - t0 : kTcMaxSamples;
+        // rows of n % 16 != 0 inputs go through a padded copy, chunk by chunk
+        const int pad_t = tc_pad_samples(c->n, c->f, c->t_max);
+        if (!pad_t && (reinterpret_cast<uintptr_t>(volt) & 15) != 0) return CORR_E_ARG;
+        const int step = pad_t ? (pad_t < kTcMaxSamples ? pad_t : kTcMaxSamples) : kTcMaxSamples;
+        for (int t0 = 0; t0 < nt; t0 += step) {
+            const int ntc = nt - t0 < step ? nt - t0 : step;
+            const uint8_t *src = volt + size_t(t0) * row;
+            int ld = 0;
+            if (pad_t) {
+                prof_begin(c, s);
+                e = launch_pad_rows(src, (long long)ntc * c->f, c->n, tc_ld(c->n), c->tc_pad, s);
+                prof_end(c, CORR_K_UNPACK, s, 1);
+                if (e != cudaSuccess) return cuda_fail(e);
+                src = c->tc_pad;
+                ld = tc_ld(c->n);
+            }
             prof_begin(c, s);
             TcOptions opt;
             opt.wait_limit = c->wait_limit;
             opt.inject_stall = c->inject_stall;
             c->inject_stall = false;
-            e = launch_xeng_tc(volt + size_t(t0) * row, c->f, c->n, ntc, zi, target, fresh,
-                               c->status, opt, s);
+            const TcArray arr{src, target, c->f, c->n, ntc, zi, fresh, tc_items(c), ld};
+            e = launch_xeng_tc_batch(&arr, 1, c->status, opt, s);
             prof_end(c, CORR_K_XENGINE, s, 1);
             if (e != cudaSuccess) return cuda_fail(e);
             fresh = false;
@@ -203,7 +240,7 @@ int accumulate_to(corr_ctx *c, const uint8_t *volt, int nt, int32_t *target, boo
         const size_t plane_max = size_t(P.f_chunk) * (P.t_chunk / 2) * P.n_pad;
         int32_t *A = reinterpret_cast<int32_t *>(c->stage);
         int32_t *W = A + plane_max;
-        const int tile = c->tile ? c->tile : (c->n <= 32 ? 32 : 64);
+        const int tile = (c->tile == 32 || c->tile == 64) ? c->tile : (c->n <= 32 ? 32 : 64);
         const int n_pad = int(round_up(size_t(c->n), size_t(tile)));
         for (int t0 = 0; t0 < nt; t0 += P.t_chunk) {
             const int ntc = nt - t0 < P.t_chunk ? nt - t0 : P.t_chunk;
@@ -392,7 +429,7 @@ int corr_set_path(corr_ctx *c, int path)
 
 int corr_set_tile(corr_ctx *c, int tile)
 {
-    if (!c || (tile != 0 && tile != 32 && tile != 64)) return ret(CORR_E_ARG);
+    if (!c || (tile != 0 && tile != 32 && tile != 64 && tile != 128 && tile != 256)) return ret(CORR_E_ARG);
     if (c->samples != 0) return ret(CORR_E_STATE);
     c->tile = tile;
     return ret(CORR_OK);
@@ -466,6 +503,7 @@ int corr_bind_workspace(corr_ctx *c, void *d_ws, size_t bytes)
     c->acc = reinterpret_cast<int32_t *>(c->ws + L.acc_off);
     c->stage = c->ws + L.stage_off;
     for (int b = 0; b < kHostBuffers; ++b) c->host_stage[b] = c->ws + L.host_off[b];
+    c->tc_pad = c->ws + L.pad_off;
     c->host_next = 0;
     c->out_pending = false;
     c->samples = 0;
@@ -883,7 +921,7 @@ int batch_correlate(corr_batch *b, const uint8_t *const *d_volt, const int *n_ti
     int tc[CORR_BATCH_MAX], n_tc = 0, max_nt = 0;
     for (int a = 0; a < b->n; ++a) {
         if (!d_volt[a] || n_time[a] == 0 || (into && !into[a])) continue;
-        if (resolve_path(b->ctx[a], b->ctx[a]->path) == CORR_PATH_TC_FP8) {
+        if (resolve_path(b->ctx[a], b->ctx[a]->path) == CORR_PATH_TC_FP8 && b->ctx[a]->n % 16 == 0) {
             tc[n_tc++] = a;
             if (n_time[a] > max_nt) max_nt = n_time[a];
         }
@@ -891,6 +929,8 @@ int batch_correlate(corr_batch *b, const uint8_t *const *d_volt, const int *n_ti
     for (int g0 = 0; g0 < n_tc; g0 += CORR_BATCH_TC_GROUP) {
         const int gn = n_tc - g0 < CORR_BATCH_TC_GROUP ? n_tc - g0 : CORR_BATCH_TC_GROUP;
         corr_ctx *lead = b->ctx[tc[g0]];
+        for (int x = 0; x < gn; ++x)
+            if ((reinterpret_cast<uintptr_t>(d_volt[tc[g0 + x]]) & 15) != 0) return CORR_E_ARG;
         if (!into) {
             // the launch writes the arrays' accumulators: order it after any host
             // dump of them that may still be copying out on an output stream
@@ -912,6 +952,7 @@ int batch_correlate(corr_batch *b, const uint8_t *const *d_volt, const int *n_ti
                 arr[k].nt = ntc;
                 arr[k].zero_invalid = (c->flags & CORR_ZERO_INVALID) != 0;
                 arr[k].fresh = t0 == 0 ? (into ? true : c->fresh) : false;
+                arr[k].items = tc_items(c);
                 ++k;
             }
             TcOptions opt;
@@ -933,7 +974,7 @@ int batch_correlate(corr_batch *b, const uint8_t *const *d_volt, const int *n_ti
     }
     for (int a = 0; a < b->n; ++a) {
         if (!d_volt[a] || n_time[a] == 0 || (into && !into[a])) continue;
-        if (resolve_path(b->ctx[a], b->ctx[a]->path) == CORR_PATH_TC_FP8) continue;
+        if (resolve_path(b->ctx[a], b->ctx[a]->path) == CORR_PATH_TC_FP8 && b->ctx[a]->n % 16 == 0) continue;
         if (into) {
             const int rc = accumulate_to(b->ctx[a], d_volt[a], n_time[a], into[a], true, s);
             if (rc != CORR_OK) return rc;

@@ -65,6 +65,11 @@ cudaError_t launch_unpack_kmajor(const uint8_t *volt, int n_chan, int n, int f0,
                                  int nt, int n_pad, int t_pad, bool zero_invalid,
                                  int8_t *out, int8_t *out_tw, cudaStream_t s);
 
+// Copy `rows` rows of n bytes (stride n in src) to a stride of ld >= n bytes
+// in dst (the tensor-core path's 16-byte row alignment); bytes between rows
+// are left as they are.
+cudaError_t launch_pad_rows(const uint8_t *src, long long rows, int n, int ld, uint8_t *dst, cudaStream_t s);
+
 // CUDA-core X-engine over a staged channel chunk; adds (or, if `fresh`,
 // stores) into acc[f0 + fl][P][2].  tile: 32 or 64 inputs per side (n_pad a
 // multiple of it).
@@ -82,19 +87,26 @@ struct TcOptions {
     long long wait_limit = 0;   // bounded-wait limit in clock64 cycles (0: about 1 s)
     bool inject_stall = false;  // test hook: make the launch's first wait expire
 };
+// Work items of the tensor-core path: single 128 x 128 tile pairs, pair items
+// (a diagonal tile and the tile left of it, sharing one conversion), or
+// pairs only on launches of at least 64 stages.
+enum class TcItems { kAuto = 0, kSingle = 1, kPairs = 2 };
 struct TcArray {
-    const uint8_t *volt;   // [nt][n_chan][n] packed voltages
+    const uint8_t *volt;   // [nt][n_chan][ld] packed voltages (n used of each row of ld bytes)
     int32_t *acc;          // [n_chan][P][2] accumulators
     int n_chan, n, nt;
     bool zero_invalid, fresh;
+    TcItems items = TcItems::kAuto;
+    int ld = 0;            // row stride in bytes, a multiple of 16 (0: n)
 };
+// Samples per padded copy for the tensor-core path when n % 16 != 0: the
+// whole integration if it fits kTcPadCap bytes, else chunks of a multiple
+// of 64 samples.
+constexpr size_t kTcPadCap = size_t(256) << 20;
 // One persistent launch over every (channel, tile pair) of up to
 // kTcMaxArrays arrays (nt <= kTcMaxSamples each; arrays with nt == 0 skipped).
 cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus *status,
                                  const TcOptions &opt, cudaStream_t s);
-cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool zero_invalid,
-                           int32_t *acc, bool fresh, DeviceStatus *status, const TcOptions &opt,
-                           cudaStream_t s);
 
 // Incoherent beam: out[k][f] = sum of |x|^2 over inputs and the n_avg samples
 // of block k (n_time / n_avg blocks), int32.

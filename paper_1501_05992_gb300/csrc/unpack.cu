@@ -16,6 +16,12 @@
 //
 // Both are HBM-bound: one byte read and 4 (words: 2 planes x 2 bytes) or 2
 // (K-major) bytes written per complex sample.
+//
+// The tensor-core path reads the packed bytes themselves, through TMA, which
+// needs rows (the n inputs of one channel and sample) that start on 16-byte
+// boundaries.  For other input counts the rows are first copied to a stride
+// of round_up(n, 16) bytes (the bytes between rows are never read: the
+// tensor map's extent is n and TMA fills columns past it with zeros).
 #include "internal.cuh"
 
 namespace corr {
@@ -177,7 +183,29 @@ int grid_for(long long total, int threads)
     return int(b);
 }
 
+// dst[row * ld + x] = src[row * n + x] for x < n: one thread per source byte,
+// reads and writes both coalesced along the row.
+__global__ void __launch_bounds__(256)
+pad_rows_kernel(const uint8_t *__restrict__ src, long long n_bytes, int n, int ld, uint8_t *__restrict__ dst)
+{
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n_bytes;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long row = e / n;
+        dst[row * ld + (e - row * n)] = __ldg(src + e);
+    }
+}
+
 }  // namespace
+
+cudaError_t launch_pad_rows(const uint8_t *src, long long rows, int n, int ld, uint8_t *dst, cudaStream_t s)
+{
+    const long long n_bytes = rows * n;
+    if (n_bytes <= 0) return cudaSuccess;
+    const long long want = (n_bytes + 255) / 256;
+    const int blocks = int(want < 152 * 32 ? want : 152 * 32);
+    pad_rows_kernel<<<blocks, 256, 0, s>>>(src, n_bytes, n, ld, dst);
+    return cudaGetLastError();
+}
 
 cudaError_t launch_unpack_words(const uint8_t *volt, int n_chan, int n, int f0, int fc,
                                 int nt, int n_pad, int tw_pad, bool zero_invalid,

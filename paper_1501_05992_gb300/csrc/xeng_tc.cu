@@ -931,7 +931,7 @@ std::mutex g_dev_mu;
 
 bool tc_supported(int n_inputs, int device)
 {
-    if (n_inputs % 16 != 0 || device < 0 || device >= 64) return false;
+    if (n_inputs < 1 || device < 0 || device >= 64) return false;
     static int cached[64] = {0};                 // 0 unknown, 1 yes, -1 no
     if (cached[device] == 0) {
         cudaDeviceProp prop;
@@ -977,7 +977,8 @@ cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus 
     for (int k = 0; k < count; ++k) {
         const TcArray &A = arrays[k];
         if (A.nt <= 0) continue;
-        if (A.nt > kTcMaxSamples || A.n < 16 || A.n % 16 != 0 || A.n_chan < 1 || !A.acc ||
+        const int ld = A.ld ? A.ld : A.n;
+        if (A.nt > kTcMaxSamples || A.n < 1 || ld < A.n || ld % 16 != 0 || A.n_chan < 1 || !A.acc ||
             (reinterpret_cast<uintptr_t>(A.volt) & 15) != 0)
             return cudaErrorInvalidValue;
     }
@@ -1007,8 +1008,11 @@ cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, in
     long long items = 0;
     for (int k = 0; k < m; ++k) {
         const TcArray &A = arrays[order[k]];
+        // extent n along the inputs: a box reaching past it (a ragged last tile)
+        // reads zero bytes, i.e. samples 0 + 0i, which cancel in the corrections
+        const cuuint64_t ld = cuuint64_t(A.ld ? A.ld : A.n);
         const cuuint64_t dims[3] = {cuuint64_t(A.n), cuuint64_t(A.n_chan), cuuint64_t(A.nt)};
-        const cuuint64_t strides[2] = {cuuint64_t(A.n), cuuint64_t(A.n) * cuuint64_t(A.n_chan)};
+        const cuuint64_t strides[2] = {ld, ld * cuuint64_t(A.n_chan)};
         const cuuint32_t box[3] = {cuuint32_t(kTile), 1u, cuuint32_t(kTc)};
         const cuuint32_t estr[3] = {1u, 1u, 1u};
         CUresult cr = enc(&maps.m[k], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(A.volt), dims,
@@ -1024,7 +1028,9 @@ cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, in
         P.n_stages = (A.nt + kTc - 1) / kTc;
         P.item_begin = int(items);
         P.fresh = A.fresh ? 1 : 0;
-        P.pairs = P.n_tiles > 1 && P.n_stages >= kPairMinStages ? 1 : 0;
+        const bool want_pairs = A.items == TcItems::kPairs ||
+                                (A.items == TcItems::kAuto && P.n_stages >= kPairMinStages);
+        P.pairs = P.n_tiles > 1 && want_pairs ? 1 : 0;
         P.per_chan = items_per_channel(P.n_tiles, P.pairs != 0);
         items += (long long)A.n_chan * P.per_chan;
     }
@@ -1044,14 +1050,6 @@ cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, in
     else
         xeng_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(maps, prm);
     return cudaGetLastError();
-}
-
-cudaError_t launch_xeng_tc(const uint8_t *volt, int n_chan, int n, int nt, bool zero_invalid,
-                           int32_t *acc, bool fresh, DeviceStatus *status, const TcOptions &opt,
-                           cudaStream_t s)
-{
-    const TcArray a{volt, acc, n_chan, n, nt, zero_invalid, fresh};
-    return launch_xeng_tc_batch(&a, 1, status, opt, s);
 }
 
 }  // namespace corr

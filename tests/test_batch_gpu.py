@@ -192,6 +192,44 @@ def test_cudacore_tiles_exact(tile, shape):
     assert np.array_equal(got, oracle.to_int32(oracle.xmac(volt)))
 
 
+@pytest.mark.parametrize("tile", [128, 256])
+def test_tc_item_shapes_exact(tile):
+    """Both tcgen05 work-item shapes forced on launches of every length (single
+    tile pairs and pair items, fresh and accumulating, 2, 3 and 5 tiles with
+    ragged last tiles), alone and as arrays of one batch with different
+    shapes."""
+    if not path_available("tc_fp8", 128):
+        pytest.skip("tc_fp8 unsupported")
+    for N, F, T in [(256, 5, 300), (272, 3, 1100), (560, 2, 700)]:
+        volt = _rand((T, F, N), N + T + tile)
+        c = corr.Correlator(N, F, T, path="tc_fp8")
+        c.set_tile(tile)
+        d = torch.from_numpy(volt).cuda()
+        c.accumulate(d[:T // 3])
+        c.accumulate(d[T // 3:])
+        got = c.dump().cpu().numpy()
+        whole = c.integrate(d).cpu().numpy()
+        c.sync()
+        c.close()
+        want = oracle.to_int32(oracle.xmac(volt))
+        assert np.array_equal(got, want), (N, F, T)
+        assert np.array_equal(whole, want), (N, F, T)
+    other = 384 - tile
+    specs = [{"n_inputs": 384, "n_chan": 3, "n_time_per_int": 400, "path": "tc_fp8", "tile": tile},
+             {"n_inputs": 256, "n_chan": 4, "n_time_per_int": 400, "path": "tc_fp8", "tile": other}]
+    _check_batch(specs, [_rand((400, 3, 384), 71), _rand((400, 4, 256), 72)])
+
+
+def test_set_tile_rejects_other_values():
+    c = corr.Correlator(64, 2, 10)
+    for bad in (1, 16, 96, 512, -1):
+        with pytest.raises(corr.CorrError):
+            c.set_tile(bad)
+    for good in (0, 32, 64, 128, 256):
+        c.set_tile(good)
+    c.close()
+
+
 def test_autotune_picks_and_caches(tmp_path):
     cache = str(tmp_path / "tune.json")
     r = autotune.tune(256, 8, 500, cache_path=cache, reps=1)
@@ -203,3 +241,21 @@ def test_autotune_picks_and_caches(tmp_path):
     assert plan[0]["path"] == r["path"] and plan[1]["path"] == small["path"]
     volts = [_rand((500, 8, 256), 51), _rand((500, 8, 16), 52)]
     _check_batch(plan, volts)
+
+
+def test_batch_with_padded_tensor_core_arrays():
+    """Arrays whose input count is not a multiple of 16 correlate on the
+    tensor-core path in launches of their own, beside the shared launch of
+    the others; accumulate, dump and whole-integration calls alike."""
+    if not path_available("tc_fp8", 65):
+        pytest.skip("tc_fp8 unsupported")
+    shapes = [(65, 4, 300), (128, 3, 300), (200, 2, 300), (9, 5, 300)]
+    specs = [{"n_inputs": n, "n_chan": f, "n_time_per_int": t, "path": "tc_fp8"} for n, f, t in shapes]
+    volts = [_rand((t, f, n), 80 + k) for k, (n, f, t) in enumerate(shapes)]
+    _check_batch(specs, volts, chunks=2)
+    b = corr.Batch(specs)
+    outs = b.integrate([torch.from_numpy(v).cuda() for v in volts])
+    b.sync()
+    for v, o in zip(volts, outs):
+        assert np.array_equal(o.cpu().numpy(), oracle.to_int32(oracle.xmac(v)))
+    b.close()

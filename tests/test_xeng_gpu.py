@@ -1,5 +1,7 @@
 """Parity of every X-engine path with the CPU oracle (bit-exact: the method is
 exact integer arithmetic, so the tolerance is zero)."""
+import ctypes
+
 import numpy as np
 import pytest
 import torch
@@ -388,3 +390,47 @@ def test_tc_pair_items_zero_invalid():
     want = oracle.to_int32(oracle.xmac(volt, zero_invalid=True))
     assert np.array_equal(correlate(volt, "tc_fp8", zero_invalid=True), want)
     assert not np.array_equal(correlate(volt, "tc_fp8"), want)      # the reading matters here
+
+
+def test_tc_any_input_count_and_auto_choice():
+    """Input counts that are not a multiple of 16 run on the tensor-core path
+    through a padded copy of the rows; AUTO takes that path from 64 inputs."""
+    if not path_available("tc_fp8", 64):
+        pytest.skip("tc_fp8 unsupported")
+    for n, want_path in [(17, "cudacore"), (63, "cudacore"), (65, "tc_fp8"), (130, "tc_fp8"), (250, "tc_fp8")]:
+        c = corr.Correlator(n, 2, 100)
+        assert c.path == want_path, (n, c.path)
+        c.close()
+    rng = np.random.default_rng(65)
+    volt = rng.integers(0, 256, (333, 3, 250), dtype=np.uint8)
+    want = oracle.to_int32(oracle.xmac(volt))
+    assert np.array_equal(correlate(volt, "auto"), want)
+    assert np.array_equal(correlate(volt, "tc_fp8", chunks=[(0, 100), (100, 333)]), want)
+    assert np.array_equal(correlate(volt, "tc_fp8", zero_invalid=True),
+                          oracle.to_int32(oracle.xmac(volt, zero_invalid=True)))
+
+
+def test_tc_padded_rows_in_chunks():
+    """17 inputs x 2048 channels x 5000 samples: the padded copy (32-byte rows)
+    holds 4096 samples, so one call is correlated in two padded chunks."""
+    if not path_available("tc_fp8", 17):
+        pytest.skip("tc_fp8 unsupported")
+    N, F, T = 17, 2048, 5000
+    rng = np.random.default_rng(17)
+    volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+    want = oracle.to_int32(oracle.xmac(volt))
+    assert np.array_equal(correlate(volt, "tc_fp8"), want)
+
+
+def test_tc_misaligned_voltages_rejected():
+    """The tensor-core path reads rows of a multiple of 16 inputs in place
+    through TMA: a voltage pointer off a 16-byte boundary is an argument error
+    and enqueues nothing."""
+    if not path_available("tc_fp8", 64):
+        pytest.skip("tc_fp8 unsupported")
+    buf = torch.zeros(64 * 3 * 20 + 8, dtype=torch.uint8, device="cuda")
+    c = corr.Correlator(64, 3, 20, path="tc_fp8")
+    lib = corr.load()
+    assert lib.corr_accumulate(c._ctx, ctypes.c_void_p(buf.data_ptr() + 8), 20, None) == corr.CORR_E_ARG
+    assert c.samples == 0
+    c.close()
