@@ -177,6 +177,22 @@ long long corr_samples(const corr_ctx *ctx);
 int corr_integrate(corr_ctx *ctx, const uint8_t *d_volt, int n_time, int32_t *d_vis, void *stream);
 
 /*
+ * corr_integrate plus the incoherent beam of the same samples (Section 3.4:
+ * the XMAC's other mode, the total power of all inputs per channel and
+ * sample, as corr_incoherent_beam computes it): d_beam (device int32
+ * [n_time / n_avg][n_chan], overwritten) gets, per channel and block of n_avg
+ * consecutive samples, the sum over inputs and samples of re^2 + im^2.  On
+ * the tensor-core path the beam is formed by the X-engine's own unpack of the
+ * voltages (no second pass over them): d_beam is zeroed on `stream`, then
+ * each 128-input tile adds its power once.  On the other paths the
+ * stand-alone beam kernel runs after the X-engine.  CORR_E_ARG on NULL
+ * d_vis or d_beam, n_avg < 1, n_time % n_avg != 0 or 128 n_avg n_inputs >=
+ * 2^31 (an int32 beam value could overflow); other errors as corr_integrate.
+ */
+int corr_integrate_beam(corr_ctx *ctx, const uint8_t *d_volt, int n_time, int32_t *d_vis, int32_t *d_beam,
+                        int n_avg, void *stream);
+
+/*
  * End-to-end variants over HOST buffers: h_volt is host memory
  * [n_time][n_chan][n_inputs] (pinned memory gives full copy bandwidth); the
  * library copies it in chunks of up to 500 samples through a ring of three

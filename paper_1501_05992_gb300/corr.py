@@ -102,6 +102,7 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_dump": ([vp, vp, vp], c_int),
             "corr_samples": ([vp], ctypes.c_longlong),
             "corr_integrate": ([vp, vp, c_int, vp, vp], c_int),
+            "corr_integrate_beam": ([vp, vp, c_int, vp, vp, c_int, vp], c_int),
             "corr_accumulate_host": ([vp, vp, c_int, vp], c_int),
             "corr_dump_host": ([vp, vp, vp], c_int),
             "corr_sync": ([vp, vp], c_int),
@@ -284,6 +285,28 @@ class Correlator:
         _check(self._lib.corr_integrate(self._ctx, vptr, nt, ctypes.c_void_p(out.data_ptr()),
                                         _stream_handle(stream)), "corr_integrate")
         return out
+
+    def integrate_beam(self, volt: torch.Tensor, n_avg: int = 1, out: torch.Tensor | None = None,
+                       beam: torch.Tensor | None = None, stream=None):
+        """integrate() plus the incoherent beam of the same samples, int32
+        [T / n_avg][F] (corr_integrate_beam): returns (triangle, beam)."""
+        nt = self._check_volt(volt, device=True)
+        if out is None:
+            out = torch.empty((self.n_chan, self.n_pairs, 2), dtype=torch.int32, device=self.device)
+        elif (out.dtype != torch.int32 or out.shape != (self.n_chan, self.n_pairs, 2)
+              or not out.is_contiguous() or out.device != self.device):
+            raise ValueError("out must be a contiguous int32 [F][P][2] tensor on the device")
+        shape = (nt // max(n_avg, 1), self.n_chan)
+        if beam is None:
+            beam = torch.empty(shape, dtype=torch.int32, device=self.device)
+        elif (beam.dtype != torch.int32 or tuple(beam.shape) != shape or not beam.is_contiguous()
+              or beam.device != self.device):
+            raise ValueError(f"beam must be a contiguous int32 {list(shape)} tensor on the device")
+        vptr = ctypes.c_void_p(volt.data_ptr()) if nt > 0 else ctypes.c_void_p(0)
+        _check(self._lib.corr_integrate_beam(self._ctx, vptr, nt, ctypes.c_void_p(out.data_ptr()),
+                                             ctypes.c_void_p(beam.data_ptr()), int(n_avg),
+                                             _stream_handle(stream)), "corr_integrate_beam")
+        return out, beam
 
     def accumulate_host(self, volt: torch.Tensor, stream=None) -> None:
         nt = self._check_volt(volt, device=False)

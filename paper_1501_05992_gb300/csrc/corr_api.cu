@@ -201,7 +201,12 @@ int wait_host_dump(corr_ctx *c, cudaStream_t s)
 // Correlate n_time samples already in device memory into the packed triangle
 // `target` (the context's accumulators, or a caller's output buffer for a
 // whole integration); fresh: the first launch stores instead of adding.
-int accumulate_to(corr_ctx *c, const uint8_t *volt, int nt, int32_t *target, bool fresh, cudaStream_t s)
+// With `beam` set, the incoherent beam of the same samples goes to beam
+// [nt / beam_avg][n_chan]: added by the tensor-core kernel's converters
+// (the caller zeroes it first), written by the stand-alone beam kernel on the
+// other paths.
+int accumulate_to(corr_ctx *c, const uint8_t *volt, int nt, int32_t *target, bool fresh, cudaStream_t s,
+                  int32_t *beam = nullptr, int beam_avg = 1)
 {
     const int path = resolve_path(c, c->path);
     const bool zi = (c->flags & CORR_ZERO_INVALID) != 0;
@@ -229,7 +234,10 @@ int accumulate_to(corr_ctx *c, const uint8_t *volt, int nt, int32_t *target, boo
             opt.wait_limit = c->wait_limit;
             opt.inject_stall = c->inject_stall;
             c->inject_stall = false;
-            const TcArray arr{src, target, c->f, c->n, ntc, zi, fresh, tc_items(c), ld};
+            TcArray arr{src, target, c->f, c->n, ntc, zi, fresh, tc_items(c), ld};
+            arr.beam = beam;
+            arr.beam_avg = beam_avg;
+            arr.beam_t0 = t0;
             e = launch_xeng_tc_batch(&arr, 1, c->status, opt, s);
             prof_end(c, CORR_K_XENGINE, s, 1);
             if (e != cudaSuccess) return cuda_fail(e);
@@ -283,6 +291,12 @@ int accumulate_to(corr_ctx *c, const uint8_t *volt, int nt, int32_t *target, boo
         }
     } else {
         return CORR_E_UNSUPPORTED;
+    }
+    if (beam && path != CORR_PATH_TC_FP8) {
+        prof_begin(c, s);
+        e = launch_beam(volt, nt, c->f, c->n, beam_avg, zi, beam, s);
+        prof_end(c, CORR_K_OTHER, s, 1);
+        if (e != cudaSuccess) return cuda_fail(e);
     }
     return CORR_OK;
 }
@@ -561,6 +575,32 @@ int corr_integrate(corr_ctx *c, const uint8_t *d_volt, int n_time, int32_t *d_vi
     }
     if (!d_volt) return ret(CORR_E_ARG);
     return ret(accumulate_to(c, d_volt, n_time, d_vis, true, s));
+}
+
+int corr_integrate_beam(corr_ctx *c, const uint8_t *d_volt, int n_time, int32_t *d_vis, int32_t *d_beam,
+                        int n_avg, void *stream)
+{
+    Range nvtx_range("corr_integrate_beam");
+    if (!c || n_time < 0 || !d_vis || !d_beam || n_avg < 1 || n_time % n_avg != 0 ||
+        (long long)n_avg * c->n * 128LL >= (1LL << 31))
+        return ret(CORR_E_ARG);
+    if (!c->ws) return ret(CORR_E_STATE);
+    if (n_time > c->t_max) return ret(CORR_E_OVERFLOW);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    if (n_time == 0) {
+        if (cudaMemsetAsync(d_vis, 0, acc_words(c) * sizeof(int32_t), s) != cudaSuccess) {
+            cudaGetLastError();
+            return ret(CORR_E_CUDA);
+        }
+        return ret(CORR_OK);
+    }
+    if (!d_volt) return ret(CORR_E_ARG);
+    if (resolve_path(c, c->path) == CORR_PATH_TC_FP8 &&
+        cudaMemsetAsync(d_beam, 0, size_t(n_time / n_avg) * size_t(c->f) * sizeof(int32_t), s) != cudaSuccess) {
+        cudaGetLastError();
+        return ret(CORR_E_CUDA);
+    }
+    return ret(accumulate_to(c, d_volt, n_time, d_vis, true, s, d_beam, n_avg));
 }
 
 long long corr_samples(const corr_ctx *c)

@@ -98,6 +98,10 @@ struct TcArray {
     bool zero_invalid, fresh;
     TcItems items = TcItems::kAuto;
     int ld = 0;            // row stride in bytes, a multiple of 16 (0: n)
+    // incoherent beam of the same samples, added into beam[(beam_t0 + t) /
+    // beam_avg][n_chan] (zeroed by the caller); NULL for none
+    int32_t *beam = nullptr;
+    int beam_avg = 1, beam_t0 = 0;
 };
 // Samples per padded copy for the tensor-core path when n % 16 != 0: the
 // whole integration if it fits kTcPadCap bytes, else chunks of a multiple

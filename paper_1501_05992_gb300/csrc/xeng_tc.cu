@@ -57,6 +57,9 @@
 //   warps 18-21 epilogue: TMEM -> int32, corrections, packed-triangle store
 //              (fp32 on exact integers; each store instruction writes 32
 //              consecutive elements of one packed row)
+//   warps 23-24 (launches that also form the incoherent beam only): the
+//              total power of each tile's inputs per sample, read from the
+//              packed bytes in shared memory and added into the beam
 // TMEM holds two accumulators (2 x 256 columns).  A single item takes the
 // next one in turn, so its epilogue overlaps the main loop of the next item; a
 // pair item takes both, its diagonal part in the one that is released first.
@@ -100,6 +103,11 @@ constexpr int kTeams = 2, kTeamWarps = kConvWarps / kTeams;   // converter teams
 static_assert(kPackedStages % kTeams == 0, "packed slots must be team-exclusive");
 constexpr int kThreads = (2 + kConvWarps + kEpiWarps + 1) * 32;   // 736: warp 22 converts, warp 17 idles
 constexpr int kFirstConvWarp = 2, kFirstEpiWarp = 2 + kConvWarps;
+// With the incoherent beam, warps 23 and 24 form it from the packed bytes in
+// shared memory (32 rows of each stage each); the registers (80 a thread)
+// leave room for exactly these two more warps.
+constexpr int kBeamWarps = 2, kFirstBeamWarp = kThreads / 32;
+constexpr int kThreadsBeam = kThreads + kBeamWarps * 32;   // 800
 constexpr int kTmemCols = 512;               // 2 accumulator slots x (128 Re + 128 Im)
 // A pair item needs both TMEM accumulators free before its first MMA, so the
 // previous item's epilogue is exposed once per pair.  On short launches that
@@ -133,6 +141,8 @@ struct ArrayParams {
     int fresh;
     int pairs;      // pair items in use (else one item per tile pair)
     int rot_step;   // item rotation per stride round (see decode_item)
+    int32_t *beam;  // incoherent beam [.][n_chan], added to (NULL: none)
+    int beam_avg, beam_t0;   // samples per beam value; the launch's first sample
 };
 
 struct Params {
@@ -396,6 +406,21 @@ __device__ __forceinline__ Item decode_item(const Params &p, int item)
     return it;
 }
 
+// 256 (r^2 + m^2) summed over the 4 packed samples of w, plus acc: the high
+// nibble with the low one cleared is the signed byte 16 r, the low nibble
+// moved up the signed byte 16 m (Appendix A: two's complement, real high).
+// With zero_invalid, samples with a nibble of 8 count as zero.
+__device__ __forceinline__ int power256(uint32_t w, bool zero_invalid, int acc)
+{
+    uint32_t hr = w & 0xF0F0F0F0u, hm = (w << 4) & 0xF0F0F0F0u;
+    if (zero_invalid) {
+        const uint32_t bad = __vcmpeq4(hr, 0x80808080u) | __vcmpeq4(hm, 0x80808080u);
+        hr &= ~bad;
+        hm &= ~bad;
+    }
+    return __dp4a(int(hm), int(hm), __dp4a(int(hr), int(hr), acc));
+}
+
 // 4 packed bytes (r << 4 | m) -> E4M3 codes u = nibble ^ 8 (value u * 2^-9).
 __device__ __forceinline__ void codes(uint32_t w, bool zero_invalid, uint32_t &R, uint32_t &M)
 {
@@ -412,8 +437,10 @@ __device__ __forceinline__ void codes(uint32_t w, bool zero_invalid, uint32_t &R
     }
 }
 
-template <bool kZeroInvalid>
-__global__ void __launch_bounds__(kThreads, 1)
+// kBeam: the converters also add the incoherent beam (Section 3.4: the total
+// power of all inputs per channel and sample) of the arrays that ask for it.
+template <bool kZeroInvalid, bool kBeam>
+__global__ void __launch_bounds__(kBeam ? kThreadsBeam : kThreads, 1)
 xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Params p)
 {
     extern __shared__ uint8_t smem_raw[];
@@ -440,7 +467,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
     if (threadIdx.x == 0) {
         for (int s = 0; s < kPackedStages; ++s) {
             mbar_init(bar_packed_full(s), 1);
-            mbar_init(bar_packed_empty(s), kTeamWarps);
+            mbar_init(bar_packed_empty(s), kTeamWarps + (kBeam ? kBeamWarps : 0));
         }
         for (int s = 0; s < kPlaneStages; ++s) {
             mbar_init(bar_plane_full(s), kTeamWarps);
@@ -459,7 +486,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
         for (int a = 0; a < p.n_arrays; ++a)
             asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&tmaps.m[a])) : "memory");
     }
-    for (int e = threadIdx.x; e < kSumsBytes / 4; e += kThreads) sums[e] = 0;
+    for (int e = threadIdx.x; e < kSumsBytes / 4; e += blockDim.x) sums[e] = 0;
     if (warp == 1) {
         asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
                      "r"(kTmemCols));
@@ -687,6 +714,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                     mbar_arrive(bar_plane_full(cstage));
                     mbar_arrive(bar_packed_empty(pstage));
                 }
+
                 // byte lanes: at most 4 stages x 4 rows of codes <= 15 (240)
                 if (++since_widen == 4) {
                     since_widen = 0;
@@ -743,6 +771,65 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
             }
             __syncwarp();
             if (lane == 0) mbar_arrive(bar_sums_full(buf));
+        }
+    } else if (kBeam && warp >= kFirstBeamWarp) {
+        // --------------------------------------------------- incoherent beam --
+        // Every tile's 128 inputs are added once per channel and sample: the
+        // B tile of each diagonal item (single items) or pair item, and for the
+        // pair item (1, 0) its A tile (0) too, which the diagonal item (0, 0)
+        // then leaves out.  Lane l owns row 32 w + l of each stage (a sample)
+        // and reads its 8 chunks rotated by l, so the 8 lanes of a quarter-warp
+        // always hit 8 different 16-byte bank groups.  The warps walk every
+        // stage of the CTA in order and release each packed slot with the
+        // converters.
+        const int bw = warp - kFirstBeamWarp;
+        const int row = bw * 32 + lane;
+        uint32_t g0 = 0;
+        bool ok = true;
+        for (int item = first_item; ok && item < p.n_items; item += item_step) {
+            const Item it = decode_item(p, item);
+            const ArrayParams &A = p.a[it.a];
+            const int n_stages = A.n_stages;
+            const bool pairs = A.pairs != 0 && A.n_tiles > 1;
+            const bool b_tile = A.beam && (it.kind == kPairItem || (it.kind == kDiagItem && !pairs));
+            const bool a_tile = A.beam && it.kind == kPairItem && it.J == 0;
+            int32_t *const beam_f = A.beam ? A.beam + it.f : nullptr;
+            for (uint32_t gg = g0; gg < g0 + uint32_t(n_stages); ++gg) {
+                const int pstage = int(gg % kPackedStages);
+                const uint32_t pphase = (gg / kPackedStages) & 1u;
+                int okw = 1;
+                if (lane == 0) okw = mbar_wait(bar_packed_full(pstage), pphase, abort, p.status, 10, p.wait_limit);
+                okw = __shfl_sync(0xFFFFFFFFu, okw, 0);
+                if (!okw) {
+                    ok = false;
+                    break;
+                }
+                (void)mbar_try(bar_packed_full(pstage), pphase);   // completed: acquire for every lane
+                const int t = int(gg - g0) * kTc + row;
+                if ((b_tile || a_tile) && t < A.nt) {
+                    const uint8_t *pk = smem + kSmPacked + pstage * kPackedStageBytes + row * 128;
+                    // four independent sums (one per word of a chunk) keep the
+                    // dp4a chains short
+                    int a0 = 0, a1 = 0, a2 = 0, a3 = 0;
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        if (half == 0 ? !b_tile : !a_tile) continue;
+                        const uint8_t *src = pk + (half == 0 ? kPackedTileBytes : 0);
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            const uint4 w = *reinterpret_cast<const uint4 *>(src + ((k + lane) & 7) * 16);
+                            a0 = power256(w.x, kZeroInvalid, a0);
+                            a1 = power256(w.y, kZeroInvalid, a1);
+                            a2 = power256(w.z, kZeroInvalid, a2);
+                            a3 = power256(w.w, kZeroInvalid, a3);
+                        }
+                    }
+                    atomicAdd(beam_f + (size_t)((A.beam_t0 + t) / A.beam_avg) * A.n_chan, (a0 + a1 + a2 + a3) >> 8);
+                }
+                __syncwarp();
+                if (lane == 0) mbar_arrive(bar_packed_empty(pstage));
+            }
+            g0 += uint32_t(n_stages);
         }
     } else if (warp >= kFirstEpiWarp && warp < kFirstEpiWarp + kEpiWarps) {
         // ------------------------------------------------------- epilogue --
@@ -960,12 +1047,11 @@ cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus 
     {
         std::lock_guard<std::mutex> lock(g_dev_mu);
         if (!g_attr_set[dev]) {
-            e = cudaFuncSetAttribute(xeng_tc_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kSmemBytes);
-            if (e != cudaSuccess) return e;
-            e = cudaFuncSetAttribute(xeng_tc_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                     kSmemBytes);
-            if (e != cudaSuccess) return e;
+            for (auto fn : {xeng_tc_kernel<false, false>, xeng_tc_kernel<true, false>, xeng_tc_kernel<false, true>,
+                            xeng_tc_kernel<true, true>}) {
+                e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, kSmemBytes);
+                if (e != cudaSuccess) return e;
+            }
             e = cudaDeviceGetAttribute(&g_sm_count[dev], cudaDevAttrMultiProcessorCount, dev);
             if (e != cudaSuccess) return e;
             g_attr_set[dev] = 1;
@@ -1032,6 +1118,9 @@ cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, in
                                 (A.items == TcItems::kAuto && P.n_stages >= kPairMinStages);
         P.pairs = P.n_tiles > 1 && want_pairs ? 1 : 0;
         P.per_chan = items_per_channel(P.n_tiles, P.pairs != 0);
+        P.beam = A.beam;
+        P.beam_avg = A.beam_avg > 0 ? A.beam_avg : 1;
+        P.beam_t0 = A.beam_t0;
         items += (long long)A.n_chan * P.per_chan;
     }
     if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
@@ -1045,10 +1134,15 @@ cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, in
         ArrayParams &P = prm.a[k];
         P.rot_step = grid % P.per_chan == 0 ? 1 : 0;
     }
+    bool beam = false;
+    for (int k = 0; k < m; ++k) beam = beam || prm.a[k].beam != nullptr;
+    const int threads = beam ? kThreadsBeam : kThreads;
     if (zero_invalid)
-        xeng_tc_kernel<true><<<grid, kThreads, kSmemBytes, s>>>(maps, prm);
+        (beam ? xeng_tc_kernel<true, true> : xeng_tc_kernel<true, false>)<<<grid, threads, kSmemBytes, s>>>(maps,
+                                                                                                           prm);
     else
-        xeng_tc_kernel<false><<<grid, kThreads, kSmemBytes, s>>>(maps, prm);
+        (beam ? xeng_tc_kernel<false, true> : xeng_tc_kernel<false, false>)<<<grid, threads, kSmemBytes, s>>>(
+            maps, prm);
     return cudaGetLastError();
 }
 

@@ -85,3 +85,47 @@ def test_remap_arguments():
         corr.remap(t)                                         # default order needs whole PFBs
     with pytest.raises(corr.CorrError):
         corr.remap(t, torch.arange(70, dtype=torch.int32, device="cuda"), f_avg=3)
+
+
+@pytest.mark.parametrize("path", ["cudacore", "mma_i8", "tc_fp8"])
+def test_integrate_beam_exact(path):
+    """corr_integrate_beam: the triangle and the incoherent beam of the same
+    samples, both equal to the oracle's; on the tensor-core path the beam
+    comes from the X-engine's own unpack (pair and single items, a padded
+    input count, block averages, the invalid-code reading)."""
+    cases = [(256, 6, 4160, 1, False), (256, 3, 700, 5, False), (384, 2, 4096, 64, True),
+             (65, 3, 300, 3, False), (128, 4, 1000, 1, True)]
+    ran = 0
+    for N, F, T, n_avg, zi in cases:
+        try:
+            c = corr.Correlator(N, F, T, path=path, zero_invalid=zi)
+        except corr.CorrError as e:
+            if e.status == corr.CORR_E_UNSUPPORTED:
+                continue
+            raise
+        rng = np.random.default_rng(N + F + T + n_avg)
+        volt = rng.integers(0, 256, (T, F, N), dtype=np.uint8)
+        d = torch.from_numpy(volt).cuda()
+        tri, beam = c.integrate_beam(d, n_avg)
+        c.sync()
+        c.close()
+        assert np.array_equal(tri.cpu().numpy(), oracle.to_int32(oracle.xmac(volt, zero_invalid=zi))), (N, F, T)
+        assert np.array_equal(beam.cpu().numpy(), oracle.beam(volt, n_avg, zero_invalid=zi)), (N, F, T, n_avg)
+        ran += 1
+    assert ran
+
+
+def test_integrate_beam_long_and_extreme():
+    """A 40000-sample integration (two tensor-core launches, the beam's second
+    half offset by the first launch's samples) of all -8-8i samples: the
+    largest power per sample, 128 per input."""
+    N, F, T = 128, 2, 40000
+    c = corr.Correlator(N, F, T, path="auto")
+    volt = np.full((T, F, N), 0x88, np.uint8)
+    volt[::3, 1, ::5] = 0x77
+    d = torch.from_numpy(volt).cuda()
+    tri, beam = c.integrate_beam(d, 8)
+    c.sync()
+    c.close()
+    assert np.array_equal(beam.cpu().numpy(), oracle.beam(volt, 8))
+    assert np.array_equal(tri.cpu().numpy(), oracle.to_int32(oracle.xmac(volt)))
