@@ -396,7 +396,7 @@ def measure_extras(arrays, volts, outs, stream_, dev, peaks, src, full=True):
         stream = torch.from_numpy(pkts.packetise(volts[0][:500].cpu().numpy(), 0)).to(dev)
         blk = torch.empty((500, f, n), dtype=torch.uint8, device=dev)
         seen = torch.empty(corr.PKT_SLOTS, dtype=torch.int32, device=dev)
-        cnt = torch.empty(6, dtype=torch.int32, device=dev)
+        cnt = torch.empty(corr.PKT_COUNTERS, dtype=torch.int32, device=dev)
         torch.cuda.synchronize(dev)
         ms = _time_ms(lambda: corr.ingest_packets(stream, 0, blk, seen, cnt, stream=stream_), stream_)
         ok = bool(torch.equal(blk, volts[0][:500])) and cnt.tolist()[0] == stream.shape[0]

@@ -564,7 +564,8 @@ def incoherent_beam(volt: torch.Tensor, n_avg: int = 1, zero_invalid: bool = Fal
 
 PKT_BYTES, PKT_FRAMES, PKT_CHANNELS, PKT_INPUTS = 264, 500, 3072, 256
 PKT_SLOTS = PKT_FRAMES * (PKT_CHANNELS // 4) * 4
-PKT_COUNTER_NAMES = ("good", "bad_header", "bad_checksum", "bad_field", "duplicate", "missing")
+PKT_COUNTER_NAMES = ("good", "bad_header", "bad_checksum", "bad_field", "duplicate", "missing", "timeout")
+PKT_COUNTERS = len(PKT_COUNTER_NAMES)
 
 
 def ingest_packets(packets: torch.Tensor, bank: int, out: torch.Tensor | None = None,
@@ -581,11 +582,12 @@ def ingest_packets(packets: torch.Tensor, bank: int, out: torch.Tensor | None = 
     if seen is None:
         seen = torch.empty(PKT_SLOTS, dtype=torch.int32, device=dev)
     if counters is None:
-        counters = torch.empty(6, dtype=torch.int32, device=dev)
+        counters = torch.empty(PKT_COUNTERS, dtype=torch.int32, device=dev)
     if tuple(out.shape) != (PKT_FRAMES, PKT_CHANNELS, PKT_INPUTS) or out.dtype != torch.uint8:
         raise ValueError("out must be uint8 [500][3072][256]")
-    if seen.numel() * seen.element_size() < PKT_SLOTS * 4 or counters.numel() < 6 or counters.dtype != torch.int32:
-        raise ValueError("seen must hold 4 bytes per slot and counters 6 int32")
+    if (seen.numel() * seen.element_size() < PKT_SLOTS * 4 or counters.numel() < PKT_COUNTERS
+            or counters.dtype != torch.int32):
+        raise ValueError(f"seen must hold 4 bytes per slot and counters {PKT_COUNTERS} int32")
     _check(load().corr_ingest_packets(ctypes.c_void_p(packets.data_ptr()), packets.shape[0], bank,
                                       ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(seen.data_ptr()),
                                       ctypes.c_void_p(counters.data_ptr()), _stream_handle(stream)),

@@ -14,6 +14,9 @@
 // and the lanes store the samples as four 64-byte runs.  Slots (frame, group
 // of four channels, PFB) no good packet filled are then written with 0x88,
 // the appendix's invalid code, which CORR_ZERO_INVALID turns into zeros.
+// A slot is marked filled with a plain store (no value comes back, so the warp
+// never waits on it), and the repeats are counted at the end as good packets
+// minus distinct filled slots.
 #include "internal.cuh"
 
 namespace corr {
@@ -70,7 +73,7 @@ ingest_kernel(const uint32_t *__restrict__ pk, long long n_packets, int bank, ui
         }
         const int cgroup = 32 * chan + 4 * mgt + grp;
         const long long slot = ((long long)frame * kGroups + cgroup) * 4 + pfb;
-        if (lane == 0 && atomicExch(seen + slot, 1u) != 0u) ++mine[CORR_PKT_DUPLICATE];
+        if (lane == 0) seen[slot] = 1u;
         ++mine[CORR_PKT_GOOD];
         // data word l holds channel f2 = l / 16, inputs 64 pfb + 4 (l % 16) .. + 3
         const long long base = ((long long)frame * kChannels + 4 * cgroup) * kInputs + 64 * pfb + 4 * (lane & 15);
@@ -115,6 +118,14 @@ ingest_missing_kernel(uint8_t *__restrict__ volt, const uint32_t *__restrict__ s
     if (threadIdx.x == 0 && block_missing) atomicAdd(counters + CORR_PKT_MISSING, block_missing);
 }
 
+// Repeated packets: every good packet fills one slot, so the repeats are the
+// good packets beyond the distinct slots filled (all slots but the missing).
+__global__ void ingest_repeats_kernel(int *__restrict__ counters)
+{
+    counters[CORR_PKT_DUPLICATE] =
+        counters[CORR_PKT_GOOD] - (CORR_PKT_SLOTS - counters[CORR_PKT_MISSING]);
+}
+
 }  // namespace
 
 cudaError_t launch_ingest(const uint8_t *packets, long long n_packets, int bank, uint8_t *volt, void *seen,
@@ -132,6 +143,9 @@ cudaError_t launch_ingest(const uint8_t *packets, long long n_packets, int bank,
         if (e != cudaSuccess) return e;
     }
     ingest_missing_kernel<<<152 * 32, kIngestThreads, 0, s>>>(volt, static_cast<const uint32_t *>(seen), counters);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return e;
+    ingest_repeats_kernel<<<1, 1, 0, s>>>(counters);
     return cudaGetLastError();
 }
 

@@ -18,7 +18,9 @@ def _ingest(packets_np, bank):
     p = torch.from_numpy(np.ascontiguousarray(packets_np).reshape(-1, 264)).cuda()
     volt, cnt = corr.ingest_packets(p, bank)
     torch.cuda.synchronize()
-    return volt.cpu().numpy(), cnt.cpu().numpy().astype(np.int64)
+    cnt = cnt.cpu().numpy().astype(np.int64)
+    assert cnt[corr.PKT_COUNTER_NAMES.index("timeout")] == 0      # no device-side wait gave up
+    return volt.cpu().numpy(), cnt[:6]                             # the oracle's six counters
 
 
 def test_golden_packet():
@@ -53,7 +55,7 @@ def test_whole_bank_round_trip_into_xengine():
     stream = pkts.packetise(block, 0)[::-1].copy()
     volt_t, cnt = corr.ingest_packets(torch.from_numpy(stream).cuda(), 0)
     torch.cuda.synchronize()
-    assert cnt.cpu().tolist() == [len(stream), 0, 0, 0, 0, 0]
+    assert cnt.cpu().tolist() == [len(stream), 0, 0, 0, 0, 0, 0]
     assert torch.equal(volt_t.cpu(), torch.from_numpy(block))
     # the ingested block is the X-engine's input as it stands
     c = corr.Correlator(256, 3072, 500)
@@ -90,3 +92,29 @@ def test_arguments():
         corr.ingest_packets(torch.zeros((3, 263), dtype=torch.uint8, device="cuda"), 0)
     with pytest.raises(corr.CorrError):
         corr.ingest_packets(torch.zeros((3, 264), dtype=torch.uint8, device="cuda"), 40)
+
+
+@pytest.mark.parametrize("offset,count", [(0, 6407), (4, 6400), (0, 31), (8, 96)])
+def test_shuffled_corrupted_repeated_and_offset_streams(offset, count):
+    """Streams of shuffled packets with corrupted checksums and headers and
+    repeated packets mixed in, starting 0, 4 or 8 bytes past a 16-byte
+    boundary: the block and every counter equal the oracle's (the repeats are
+    counted as good packets beyond the distinct slots they filled)."""
+    rng = np.random.default_rng(offset * 1000 + count)
+    block = rng.integers(0, 256, (500, 3072, 256), dtype=np.uint8)
+    full = pkts.packetise(block, 1)
+    idx = rng.choice(len(full), count, replace=False)
+    sel = full[idx].copy()
+    sel[::97, 100] ^= 0x40                       # bad checksums
+    sel[::131, 0] = 0x09                         # bad headers
+    sel = np.concatenate([sel, sel[:5]])         # repeats
+    raw = torch.zeros(sel.size + offset, dtype=torch.uint8, device="cuda")
+    raw[offset:] = torch.from_numpy(sel.reshape(-1)).cuda()
+    p = raw[offset:].view(-1, 264)
+    assert (p.data_ptr() - raw.data_ptr()) == offset
+    volt, cnt = corr.ingest_packets(p, 1)
+    torch.cuda.synchronize()
+    want_v, want_c = oracle.ingest(sel, 1)
+    got = cnt.cpu().numpy().astype(np.int64)
+    assert np.array_equal(got[:6], want_c) and got[6] == 0
+    assert np.array_equal(volt.cpu().numpy(), want_v)
