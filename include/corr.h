@@ -384,9 +384,7 @@ int corr_incoherent_beam(const uint8_t *d_volt, int n_time, int n_chan, int n_in
  * mgt_frame >= 500, or sec_tick on a packet other than the second's first),
  * repeated slots (a repeated packet's bytes replace the earlier ones), and
  * slots (frame, four channels, PFB) no good packet filled, whose 256 bytes
- * are written as 0x88 (code 8 in both parts: invalid, see CORR_ZERO_INVALID),
- * and device-side waits for packet copies that gave up after about a second
- * (0 in normal operation; the bank is then incomplete).
+ * are written as 0x88 (code 8 in both parts: invalid, see CORR_ZERO_INVALID).
  * Asynchronous; allocates nothing.
  */
 #define CORR_PKT_BYTES 264
@@ -401,8 +399,7 @@ int corr_incoherent_beam(const uint8_t *d_volt, int n_time, int n_chan, int n_in
 #define CORR_PKT_BAD_FIELD 3
 #define CORR_PKT_DUPLICATE 4
 #define CORR_PKT_MISSING 5
-#define CORR_PKT_TIMEOUT 6
-#define CORR_PKT_COUNTERS 7
+#define CORR_PKT_COUNTERS 6
 int corr_ingest_packets(const uint8_t *d_packets, long long n_packets, int bank, uint8_t *d_volt, void *d_seen,
                         int32_t *d_counters, void *stream);
 

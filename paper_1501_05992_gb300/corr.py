@@ -564,7 +564,7 @@ def incoherent_beam(volt: torch.Tensor, n_avg: int = 1, zero_invalid: bool = Fal
 
 PKT_BYTES, PKT_FRAMES, PKT_CHANNELS, PKT_INPUTS = 264, 500, 3072, 256
 PKT_SLOTS = PKT_FRAMES * (PKT_CHANNELS // 4) * 4
-PKT_COUNTER_NAMES = ("good", "bad_header", "bad_checksum", "bad_field", "duplicate", "missing", "timeout")
+PKT_COUNTER_NAMES = ("good", "bad_header", "bad_checksum", "bad_field", "duplicate", "missing")
 PKT_COUNTERS = len(PKT_COUNTER_NAMES)
 
 

@@ -18,9 +18,7 @@ def _ingest(packets_np, bank):
     p = torch.from_numpy(np.ascontiguousarray(packets_np).reshape(-1, 264)).cuda()
     volt, cnt = corr.ingest_packets(p, bank)
     torch.cuda.synchronize()
-    cnt = cnt.cpu().numpy().astype(np.int64)
-    assert cnt[corr.PKT_COUNTER_NAMES.index("timeout")] == 0      # no device-side wait gave up
-    return volt.cpu().numpy(), cnt[:6]                             # the oracle's six counters
+    return volt.cpu().numpy(), cnt.cpu().numpy().astype(np.int64)
 
 
 def test_golden_packet():
@@ -55,7 +53,7 @@ def test_whole_bank_round_trip_into_xengine():
     stream = pkts.packetise(block, 0)[::-1].copy()
     volt_t, cnt = corr.ingest_packets(torch.from_numpy(stream).cuda(), 0)
     torch.cuda.synchronize()
-    assert cnt.cpu().tolist() == [len(stream), 0, 0, 0, 0, 0, 0]
+    assert cnt.cpu().tolist() == [len(stream), 0, 0, 0, 0, 0]
     assert torch.equal(volt_t.cpu(), torch.from_numpy(block))
     # the ingested block is the X-engine's input as it stands
     c = corr.Correlator(256, 3072, 500)
@@ -116,5 +114,5 @@ def test_shuffled_corrupted_repeated_and_offset_streams(offset, count):
     torch.cuda.synchronize()
     want_v, want_c = oracle.ingest(sel, 1)
     got = cnt.cpu().numpy().astype(np.int64)
-    assert np.array_equal(got[:6], want_c) and got[6] == 0
+    assert np.array_equal(got, want_c)
     assert np.array_equal(volt.cpu().numpy(), want_v)
