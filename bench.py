@@ -40,11 +40,6 @@ sys.path.insert(0, ROOT)
 METRIC = "Correlator CMAC/s and ×real-time, 256 inputs×3072 ch; TC vs CUDA-core, bit-exact"
 UNIT = "CMAC/s"
 SAMPLE_RATE_HZ = 1.0e4            # 10 kHz fine channels: one sample per channel per 100 us
-# register-resident probe rates on GB300 at 2070 MHz (used as the roofline of
-# the two non-tcgen05 paths): dp4a issue rate per SM per clock, and mma.sync
-# m16n8k32 s8 throughput
-DP4A_PER_SM_CLOCK = 64
-MMA_S8_TOPS_MEASURED = 158.0
 
 WORKLOADS = {
     # name: arrays [(n_inputs, n_chan, samples per integration)], integrations per step, seed
@@ -324,30 +319,63 @@ def measured_traffic(kernel_src: str, profile_md: str, workload: str):
     return float(t.group(1))
 
 
-def roofline_for(path, ops_per_launch, avg_ms, peaks, src, sm_count):
+_PROBES: dict = {}
+
+
+def measured_probes(dev) -> dict:
+    """Peak rates of the instruction forms the kernels use, measured on this
+    device by the library's probes (corr_probe_rate), in Tops/s, with the SM
+    clock sampled while they ran.  Taken once per process."""
+    if _PROBES:
+        return _PROBES
+    from paper_1501_05992_gb300 import corr
+    clk = ClockSampler(dev.index or 0)
+    clk.start()
+    clk.mark_start()
+    for kind in ("tc_fp8", "mma_s8", "dp4a", "ffma"):
+        try:
+            rate, ms = corr.probe_rate(kind)
+            _PROBES[kind] = {"tops": rate / 1e12, "ms": ms}
+        except corr.CorrError as e:
+            _PROBES[kind] = {"tops": None, "error": str(e)}
+    clk.mark_stop()
+    c = clk.stop()
+    _PROBES["clocks"] = c
+    return _PROBES
+
+
+def roofline_for(path, ops_per_launch, avg_ms, peaks, src, sm_count, probes=None):
     achieved = ops_per_launch / (avg_ms * 1e-3) / 1e12          # Tops/s
+    probes = probes or {}
     if path == "tc_fp8":
         # fp8 dense = 2 x bf16 (the nominal ratio) x the measured bf16 burst
         # rate: the X-engine launch lasts about 2 ms, far shorter than the
         # seconds-long loop the sustained figure comes from
         peak = peaks["bf16_tflops"] * 2.0
-        return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak,
-                "peak_note": f"fp8 dense = 2 x bf16 burst ({src}); ops = 8 per useful CMAC"}
+        out = {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+               "frac": achieved / peak,
+               "peak_note": f"fp8 dense = 2 x bf16 burst ({src}); ops = 8 per useful CMAC"}
+        pr = (probes.get("tc_fp8") or {}).get("tops")
+        if pr:
+            out["probe_peak"] = pr
+            out["frac_of_probe"] = achieved / pr
+            out["probe_note"] = ("tcgen05.mma kind::f8f6f4 M128 N256 K32 back to back from shared memory, "
+                                 "one issuing thread per SM (corr_probe_rate), sampled SM clock %s MHz"
+                                 % ((probes.get("clocks") or {}).get("sm_mhz")))
+        return out
     if path == "mma_i8":
         # int8 tensor rates on this part are far below 2 x bf16; the peak is
         # the measured rate of back-to-back mma.sync m16n8k32 s8 in registers
-        peak = MMA_S8_TOPS_MEASURED
+        peak = (probes.get("mma_s8") or {}).get("tops")
         return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TOPS",
-                "frac": achieved / peak,
-                "peak_note": "measured mma.sync s8 peak (register-resident probe); ops = 8 per useful CMAC"}
-    # dp4a: the integer pipe issues 16 lanes per scheduler per clock (64 per
-    # SM, measured with a register-resident probe); 8 ops per dp4a
-    peak = sm_count * DP4A_PER_SM_CLOCK * 8 * peaks.get("sm_max_mhz", 2070.0) * 1e6 / 1e12
+                "frac": achieved / peak if peak else None,
+                "peak_note": "mma.sync m16n8k32 s8 on registers, measured in this run (corr_probe_rate); "
+                             "ops = 8 per useful CMAC"}
+    # dp4a: the measured rate of register-resident dp4a (8 ops each)
+    peak = (probes.get("dp4a") or {}).get("tops")
     return {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TOPS",
-            "frac": achieved / peak,
-            "peak_note": f"{sm_count} SMs x {DP4A_PER_SM_CLOCK} dp4a per clock (measured issue rate) x 8 ops "
-                         f"at {peaks.get('sm_max_mhz', 2070.0):.0f} MHz"}
+            "frac": achieved / peak if peak else None,
+            "peak_note": "dp4a on registers, measured in this run (corr_probe_rate); 8 ops per dp4a"}
 
 
 def _time_ms(fn, stream, reps=5):
@@ -419,6 +447,7 @@ def measure_extras(arrays, volts, outs, stream_, dev, peaks, src, full=True):
         res["fine_pfb"] = measure_fine_pfb(n, f // 128, t, stream_, dev)
     sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
     res["paths_one_integration"] = measure_paths(n, f, t, volt, stream_, dev, peaks, sm_count)
+    res["beam_fused"] = measure_beam_fused(n, f, t, volt, stream_, dev)
     torch.cuda.empty_cache()
     if full:
         res["uneven_batch"] = measure_uneven_batch(stream_, dev, peaks, sm_count)
@@ -457,7 +486,7 @@ def measure_paths(n, f, t, volt, stream_, dev, peaks, sm_count):
         c.sync(stream_)
         c.close()
         tri[path] = dst
-        roof = roofline_for(path, 8.0 * cmac, ms, peaks, "measured", sm_count)
+        roof = roofline_for(path, 8.0 * cmac, ms, peaks, "measured", sm_count, measured_probes(dev))
         out[path] = {"ms_per_integration": ms, "value": cmac / (ms * 1e-3), "unit": "CMAC/s",
                      "x_real_time": t / SAMPLE_RATE_HZ / (ms * 1e-3),
                      "achieved": roof["achieved"], "peak": roof["peak"], "frac": roof["frac"],
@@ -476,6 +505,33 @@ def measure_paths(n, f, t, volt, stream_, dev, peaks, sm_count):
                          f"{f} channels, and against the oracle on whole channels {chans}")
     del tri
     return out
+
+
+def measure_beam_fused(n, f, t, volt, stream_, dev):
+    """One integration with its incoherent beam: the X-engine alone, the
+    X-engine forming the beam from its own unpack (corr_integrate_beam), and
+    the X-engine followed by the stand-alone beam pass; the fused beam must
+    equal the stand-alone one and the oracle's on sampled channels."""
+    import torch
+    import oracle
+    from paper_1501_05992_gb300 import corr
+    c = corr.Correlator(n, f, t, device=dev)
+    tri = torch.empty((f, n * (n + 1) // 2, 2), dtype=torch.int32, device=dev)
+    fused = torch.empty((t, f), dtype=torch.int32, device=dev)
+    alone = torch.empty((t, f), dtype=torch.int32, device=dev)
+    ms_x = _time_ms(lambda: c.integrate(volt, tri, stream=stream_), stream_, reps=5)
+    ms_f = _time_ms(lambda: c.integrate_beam(volt, 1, tri, fused, stream=stream_), stream_, reps=5)
+    ms_s = _time_ms(lambda: (c.integrate(volt, tri, stream=stream_),
+                             corr.incoherent_beam(volt, 1, out=alone, stream=stream_)), stream_, reps=5)
+    c.sync(stream_)
+    c.close()
+    chans = [0, f // 2, f - 1]
+    want = oracle.beam(volt[:, chans].cpu().numpy())
+    exact = bool(torch.equal(fused, alone)) and bool((fused[:, chans].cpu().numpy() == want).all())
+    return {"xengine_ms": ms_x, "fused_ms": ms_f, "separate_ms": ms_s, "fused_added_ms": ms_f - ms_x,
+            "separate_added_ms": ms_s - ms_x, "exact": exact,
+            "exact_note": f"fused beam equal to the stand-alone kernel's on all {f} channels and to the "
+                          f"oracle's on channels {chans}"}
 
 
 def measure_uneven_batch(stream_, dev, peaks, sm_count):
@@ -515,14 +571,14 @@ def measure_uneven_batch(stream_, dev, peaks, sm_count):
         del o1
         chans = [0, f - 1]
         exact = bool((outs[a][chans].cpu().numpy() == _oracle_channels(volts[a], chans)).all())
-        roof = roofline_for(spec["path"], 8.0 * cmac, ms, peaks, "measured", sm_count)
+        roof = roofline_for(spec["path"], 8.0 * cmac, ms, peaks, "measured", sm_count, measured_probes(dev))
         res["arrays"].append({
             "n_inputs": n, "n_chan": f, "samples": t, "path": spec["path"], "tile": spec["tile"],
             "autotune_ms": tuned[a]["ms"], "ms_alone": ms, "value_alone": cmac / (ms * 1e-3),
             "frac_alone": roof["frac"], "same_as_in_batch": same, "exact": exact,
             "exact_channels": chans})
     roof = roofline_for("tc_fp8" if all(p == "tc_fp8" for p in batch.paths) else batch.paths[0],
-                        8.0 * cmac_all, ms_all, peaks, "measured", sm_count)
+                        8.0 * cmac_all, ms_all, peaks, "measured", sm_count, measured_probes(dev))
     res.update({"ms_batch": ms_all, "value": cmac_all / (ms_all * 1e-3), "unit": "CMAC/s",
                 "achieved": roof["achieved"], "peak": roof["peak"], "frac": roof["frac"],
                 "exact": all(x["exact"] and x["same_as_in_batch"] for x in res["arrays"]),
@@ -612,12 +668,16 @@ def measure_fine_pfb(n, n_coarse, frames, stream_, dev):
     units = n_coarse * n * frames
     flops = units * (taps * 128 * 4 + 5 * 128 * 7)
     sm = torch.cuda.get_device_properties(dev).multi_processor_count
-    peak = sm * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    derived = sm * FP32_LANES_PER_SM * 2 * 2.070e9 / 1e12
+    probe = (measured_probes(dev).get("ffma") or {}).get("tops")
+    peak = probe or derived
     tflops = flops / ms / 1e9
     out = {"ms": ms, "frames": frames, "coarse_channels": n_coarse, "inputs": n,
            "x_real_time": frames / SAMPLE_RATE_HZ / (ms * 1e-3), "tflops": tflops, "peak_tflops": peak,
            "frac": tflops / peak, "bound": "alu",
-           "peak_note": f"{sm} SMs x {FP32_LANES_PER_SM} fp32 lanes x 2 flops x 2.07 GHz",
+           "peak_note": ("fp32 FMA on registers measured in this run (corr_probe_rate)" if probe else
+                         f"{sm} SMs x {FP32_LANES_PER_SM} fp32 lanes x 2 flops x 2.07 GHz"),
+           "derived_peak_tflops": derived, "frac_of_derived": tflops / derived,
            "bytes": x.numel() + volt.numel()}
     del x, volt
     return out
@@ -754,7 +814,7 @@ def run_ours(args, world, rank, local):
     ops_per_launch = 8.0 * step_cmac / max(1, xe_per_step)
     avg_ms = xe_ms / max(1, xe_timed)
     main_path = paths[max(range(len(arrays)), key=lambda a: arrays[a][0] ** 2 * arrays[a][1] * arrays[a][2])]
-    roof = roofline_for(main_path, ops_per_launch, avg_ms, peaks, src, sm_count)
+    roof = roofline_for(main_path, ops_per_launch, avg_ms, peaks, src, sm_count, measured_probes(dev))
     roof["traffic"] = (measured_traffic(os.path.join(ROOT, "paper_1501_05992_gb300", "csrc", "xeng_tc.cu"),
                                         os.path.join(ROOT, "profiles", "xeng_tc_coarse_channel.md"),
                                         args.workload) if main_path == "tc_fp8" else None)

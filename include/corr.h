@@ -533,6 +533,26 @@ const char *corr_strerror(int status);  /* static string, never NULL         */
 /* Library version as 10000*major + 100*minor + patch. */
 int corr_version(void);
 
+/* ---------------------------------------------------------------- probes -- */
+
+/* Peak-rate probes: the rates the X-engine forms are measured against
+ * (Section 3.4.2 compares the kernel with the GPU's peak; Eq. 4 sets the
+ * intensity needed to reach it), taken on the device instead of assumed.
+ * Each launches one block per SM running a fixed loop on register- or
+ * shared-memory-resident values: */
+#define CORR_PROBE_TC_FP8 0  /* tcgen05.mma kind::f8f6f4 E4M3 -> F32, M128 N256 K32, operands in SMEM  */
+#define CORR_PROBE_MMA_S8 1  /* mma.sync m16n8k32 s8 -> s32 on registers                               */
+#define CORR_PROBE_DP4A 2    /* dp4a (8 ops: four multiply-adds) on registers                          */
+#define CORR_PROBE_FFMA 3    /* fp32 FMA (2 ops) on registers                                         */
+/* *ops_per_s: dense ops per second of the whole device (2 per multiply-add);
+ * *launch_ms (may be NULL): the timed launch's CUDA-event time.  Runs a
+ * warm-up launch and a timed one on `stream` and waits for them (the only
+ * call here that synchronises the host besides corr_sync and the state
+ * calls).  CORR_E_ARG on a bad kind or NULL ops_per_s; CORR_E_UNSUPPORTED
+ * for CORR_PROBE_TC_FP8 off sm_103; CORR_E_TIMEOUT if the tensor-core
+ * probe's completion wait gave up.  Allocates nothing. */
+int corr_probe_rate(int kind, double *ops_per_s, double *launch_ms, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -137,6 +137,8 @@ def load(build_if_missing: bool = True) -> ctypes.CDLL:
             "corr_last_error": ([], c_int),
             "corr_strerror": ([c_int], ctypes.c_char_p),
             "corr_version": ([], c_int),
+            "corr_probe_rate": ([c_int, ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_double), vp],
+                                c_int),
         }
         for name, (args, res) in sig.items():
             fn = getattr(lib, name)
@@ -680,3 +682,15 @@ def unpack(volt: torch.Tensor, zero_invalid: bool = False, stream=None) -> torch
                               ctypes.c_void_p(out.data_ptr()), ZERO_INVALID if zero_invalid else 0,
                               _stream_handle(stream)), "corr_unpack")
     return out
+
+
+PROBES = {"tc_fp8": 0, "mma_s8": 1, "dp4a": 2, "ffma": 3}
+
+
+def probe_rate(kind: str, stream=None) -> tuple[float, float]:
+    """Measured peak rate of one instruction form on the current device
+    (corr_probe_rate): (ops per second, ms of the timed launch)."""
+    rate, ms = ctypes.c_double(), ctypes.c_double()
+    _check(load().corr_probe_rate(PROBES[kind], ctypes.byref(rate), ctypes.byref(ms), _stream_handle(stream)),
+           f"corr_probe_rate({kind})")
+    return rate.value, ms.value

@@ -930,18 +930,8 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                     int2 *const p0 = colp + (size_t)(unsigned(ic) * unsigned(ic + 1) / 2u);
                     const bool full = ic + 7 < n_in && (!dpart || c0 >= 32 * q + 32);
                     int2 v[8];
-                    if (!fresh) {
-                        int2 *pk = p0;
 #pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const bool use = full || (ic + k < n_in && (!dpart || il <= c0 + k));
-                            v[k] = use ? *pk : make_int2(0, 0);
-                            pk += ic + k + 1;
-                        }
-                    } else {
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) v[k] = make_int2(0, 0);
-                    }
+                    for (int k = 0; k < 8; ++k) v[k] = make_int2(0, 0);
                     tmem_wait_ld();
 #pragma unroll
                     for (int k = 0; k < 8; k += 2) {
@@ -954,7 +944,19 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                             __float_as_int(fmaf(__uint_as_float(vim[k + 1]), -262144.0f, c.w) + row_im) - 0x4B400000;
                     }
                     int2 *pk = p0;
-                    if (full) {
+                    if (!fresh) {
+                        // a launch that adds into the output: the integer adds are done
+                        // in L2 (red), so no warp waits on reading the eight scattered
+                        // row pieces of a chunk back first
+#pragma unroll
+                        for (int k = 0; k < 8; ++k) {
+                            if (full || (ic + k < n_in && (!dpart || il <= c0 + k))) {
+                                asm volatile("red.global.add.s32 [%0], %1;" ::"l"(&pk->x), "r"(v[k].x) : "memory");
+                                asm volatile("red.global.add.s32 [%0], %1;" ::"l"(&pk->y), "r"(v[k].y) : "memory");
+                            }
+                            pk += ic + k + 1;
+                        }
+                    } else if (full) {
 #pragma unroll
                         for (int k = 0; k < 8; ++k) {
                             *pk = v[k];

@@ -110,3 +110,12 @@ def test_fine_pfb_rejects_bad_arguments_without_touching_a_device(lib_path):
     ]
     for args, want in cases:
         assert lib.corr_fine_pfb(*args) == want, args
+
+
+def test_probe_rejects_bad_kind_without_touching_a_device(lib_path):
+    import ctypes as ct
+    lib = corr.load()
+    rate = ct.c_double()
+    assert lib.corr_probe_rate(7, ct.byref(rate), None, None) == corr.CORR_E_ARG
+    assert lib.corr_probe_rate(-1, ct.byref(rate), None, None) == corr.CORR_E_ARG
+    assert lib.corr_probe_rate(0, None, None, None) == corr.CORR_E_ARG

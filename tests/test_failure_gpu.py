@@ -60,3 +60,4 @@ def test_batch_stall_reported_by_batch_sync():
     outs = b.dump()
     b.sync()
     assert not outs[0].any() and not outs[1].any()
+
