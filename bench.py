@@ -45,6 +45,8 @@ WORKLOADS = {
     # name: arrays [(n_inputs, n_chan, samples per integration)], integrations per step, seed
     "full_band": ([(256, 3072, 5000)], 16, 1503),
     "coarse_channel": ([(256, 128, 5000)], 1, 1502),
+    # one integration of the full band (3.9 GB of voltages): a small case for traffic captures
+    "integration": ([(256, 3072, 5000)], 1, 1503),
     "uneven_batch": ([(128, 1536, 2000), (256, 3072, 5000), (1024, 512, 10000)], 1, 1504),
     # one 50 ms bank of the full band (the packet ingest's unit): a small case for profiles
     "bank": ([(256, 3072, 500)], 1, 1506),
@@ -816,7 +818,7 @@ def run_ours(args, world, rank, local):
     main_path = paths[max(range(len(arrays)), key=lambda a: arrays[a][0] ** 2 * arrays[a][1] * arrays[a][2])]
     roof = roofline_for(main_path, ops_per_launch, avg_ms, peaks, src, sm_count, measured_probes(dev))
     roof["traffic"] = (measured_traffic(os.path.join(ROOT, "paper_1501_05992_gb300", "csrc", "xeng_tc.cu"),
-                                        os.path.join(ROOT, "profiles", "xeng_tc_coarse_channel.md"),
+                                        os.path.join(ROOT, "profiles", "xeng_tc_full_band_traffic.md"),
                                         args.workload) if main_path == "tc_fp8" else None)
     roof["kernel"] = {"cudacore": "xeng_dp4a_kernel", "mma_i8": "xeng_mma8_kernel",
                       "tc_fp8": "xeng_tc_kernel"}[main_path]
