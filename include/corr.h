@@ -543,7 +543,7 @@ int corr_version(void);
 #define CORR_PROBE_TC_FP8 0  /* tcgen05.mma kind::f8f6f4 E4M3 -> F32, M128 N256 K32, operands in SMEM  */
 #define CORR_PROBE_MMA_S8 1  /* mma.sync m16n8k32 s8 -> s32 on registers                               */
 #define CORR_PROBE_DP4A 2    /* dp4a (8 ops: four multiply-adds) on registers                          */
-#define CORR_PROBE_FFMA 3    /* fp32 FMA (2 ops) on registers                                         */
+#define CORR_PROBE_FFMA 3    /* paired fp32 FMA (2 multiply-adds, 4 ops) on registers                 */
 /* *ops_per_s: dense ops per second of the whole device (2 per multiply-add);
  * *launch_ms (may be NULL): the timed launch's CUDA-event time.  Runs a
  * warm-up launch and a timed one on `stream` and waits for them (the only

@@ -9,8 +9,9 @@
 //                 accumulators per warp (the int8 X-engine's instruction)
 //   dp4a          four-way int8 dot products on registers, eight independent
 //                 chains per thread (the CUDA-core X-engine's instruction)
-//   fp32 FMA      eight independent chains per thread (the fine filterbank's
-//                 arithmetic)
+//   fp32 FMA      paired fp32 FMAs (two multiply-adds an instruction, the fine
+//                 filterbank's form), eight independent chains per thread
+// The dp4a and FMA loops are unrolled so that loop overhead stays below 2 %.
 //
 // Every kernel runs one block per SM for a fixed number of iterations on
 // values that stay in registers or shared memory; a sink store that never
@@ -117,6 +118,8 @@ __global__ void __launch_bounds__(1024) probe_mma_s8_kernel(int seed)
     if (x == 0x7fedcba1) g_probe_sink[0] = x;
 }
 
+constexpr int kUnroll = 8;                      // loop bodies per iteration: loop overhead below 2 %
+
 __global__ void __launch_bounds__(1024) probe_dp4a_kernel(int seed)
 {
     int acc[8];
@@ -124,9 +127,11 @@ __global__ void __launch_bounds__(1024) probe_dp4a_kernel(int seed)
 #pragma unroll
     for (int c = 0; c < 8; ++c) acc[c] = c;
 #pragma unroll 1
-    for (int k = 0; k < kRegIters; ++k) {
+    for (int k = 0; k < kRegIters / kUnroll; ++k) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = __dp4a(a + c, b, acc[c]);
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = __dp4a(a + c, b, acc[c]);
     }
     int x = 0;
 #pragma unroll
@@ -134,20 +139,24 @@ __global__ void __launch_bounds__(1024) probe_dp4a_kernel(int seed)
     if (x == 0x7fedcba1) g_probe_sink[1] = x;
 }
 
+// paired fp32 FMAs (one instruction, two multiply-adds), as the filterbank uses
 __global__ void __launch_bounds__(1024) probe_ffma_kernel(float seed)
 {
-    float acc[8];
-    const float a = seed * 0.999f, b = 1.0f / (seed + float(threadIdx.x));
+    float2 acc[8];
+    const float2 a = make_float2(seed * 0.999f, seed * 0.998f);
+    const float2 b = make_float2(1.0f / (seed + float(threadIdx.x)), 0.5f / (seed + float(threadIdx.x)));
 #pragma unroll
-    for (int c = 0; c < 8; ++c) acc[c] = float(c);
+    for (int c = 0; c < 8; ++c) acc[c] = make_float2(float(c), float(c) + 0.5f);
 #pragma unroll 1
-    for (int k = 0; k < kRegIters; ++k) {
+    for (int k = 0; k < kRegIters / kUnroll; ++k) {
 #pragma unroll
-        for (int c = 0; c < 8; ++c) acc[c] = fmaf(acc[c], a, b);
+        for (int u = 0; u < kUnroll; ++u)
+#pragma unroll
+            for (int c = 0; c < 8; ++c) acc[c] = __ffma2_rn(acc[c], a, b);
     }
     float x = 0.f;
 #pragma unroll
-    for (int c = 0; c < 8; ++c) x += acc[c];
+    for (int c = 0; c < 8; ++c) x += acc[c].x + acc[c].y;
     if (x == 1234.5f) g_probe_sink[2] = 1;
 }
 
@@ -184,7 +193,7 @@ extern "C" int corr_probe_rate(int kind, double *ops_per_s, double *launch_ms, v
             break;
         default:
             probe_ffma_kernel<<<sms, 1024, 0, s>>>(1.5f);
-            ops = double(sms) * 1024 * kRegIters * 8 * 2.0;
+            ops = double(sms) * 1024 * kRegIters * 8 * 2 * 2.0;
             break;
         }
     };
