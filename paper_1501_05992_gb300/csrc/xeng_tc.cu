@@ -916,11 +916,17 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 const uint32_t taddr = tmem + uint32_t(sl * 256) + (uint32_t(q * 32) << 16);
                 const int i0 = it.I * kTile;
                 // in the diagonal part, column b holds output row i0 + b, whose
-                // columns j <= i: chunks wholly left of this warp's lanes are skipped
+                // columns j <= i: chunks wholly left of this warp's lanes are skipped;
+                // in a launch that stores, warp 0 leaves its blocks of rows 64-127 to
+                // warps 2 and 3 (below), so that no warp drains more than 12 of the
+                // part's 40 chunk-columns (a launch that adds keeps every add coalesced;
+                // the beam variant, bound by its beam warps, keeps its registers)
+                const bool split = !kBeam && dpart && fresh;
                 const int c_first = dpart ? ((32 * q) & ~7) : 0;
+                const int c_last = split && q == 0 ? 64 : kTile;
                 int2 *const colp = reinterpret_cast<int2 *>(acc) + out_f + j;
 #pragma unroll 1
-                for (int c0 = c_first; c0 < kTile && i0 + c0 < n_in; c0 += 8) {
+                for (int c0 = c_first; c0 < c_last && i0 + c0 < n_in; c0 += 8) {
                     uint32_t vre[8], vim[8];
                     tmem_ld8(taddr + c0, vre);
                     tmem_ld8(taddr + 128 + c0, vim);
@@ -967,6 +973,49 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                         for (int k = 0; k < 8; ++k) {
                             if (ic + k < n_in && (!dpart || il <= c0 + k)) *pk = v[k];
                             pk += ic + k + 1;
+                        }
+                    }
+                }
+                if (split && q >= 2 && i0 + 32 * q < n_in) {
+                    // rows 32 q .. 32 q + 31, columns 0-31 of the diagonal block from this
+                    // warp's own lanes: here TMEM lane a is output row i and column b output
+                    // column j < 32 <= i, and D[a][b] = V_ij itself (Im with the other sign
+                    // of the D terms); each lane writes 8 consecutive elements of its row.
+                    // The TMEM loads are warp-wide: the condition above is the warp's,
+                    // the one below each lane's
+                    const int i = i0 + il;
+                    const bool live = i < n_in;
+                    const float rrow_im = float(-8 * Da) + 12582912.0f;
+                    int2 *const rowp = reinterpret_cast<int2 *>(acc) + out_f + (size_t)i * (i + 1) / 2 + i0;
+#pragma unroll 1
+                    for (int c0 = 0; c0 < 32; c0 += 8) {
+                        uint32_t vre[8], vim[8];
+                        tmem_ld8(taddr + c0, vre);
+                        tmem_ld8(taddr + 128 + c0, vim);
+                        tmem_wait_ld();
+                        int2 v[8];
+#pragma unroll
+                        for (int k = 0; k < 8; k += 2) {
+                            const float4 c = col[(c0 + k) >> 1];
+                            v[k].x = __float_as_int(fmaf(__uint_as_float(vre[k]), 262144.0f, c.x) + row_re) - 0x4B400000;
+                            v[k].y = __float_as_int(fmaf(__uint_as_float(vim[k]), 262144.0f, -c.y) + rrow_im) - 0x4B400000;
+                            v[k + 1].x =
+                                __float_as_int(fmaf(__uint_as_float(vre[k + 1]), 262144.0f, c.z) + row_re) - 0x4B400000;
+                            v[k + 1].y =
+                                __float_as_int(fmaf(__uint_as_float(vim[k + 1]), 262144.0f, -c.w) + rrow_im) - 0x4B400000;
+                        }
+                        int2 *const dst = rowp + c0;
+                        if (!live) {
+                        } else if ((reinterpret_cast<uintptr_t>(dst) & 15) == 0) {
+#pragma unroll
+                            for (int k = 0; k < 8; k += 2)
+                                *reinterpret_cast<int4 *>(dst + k) = make_int4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
+                        } else {
+                            dst[0] = v[0];
+#pragma unroll
+                            for (int k = 1; k < 7; k += 2)
+                                *reinterpret_cast<int4 *>(dst + k) = make_int4(v[k].x, v[k].y, v[k + 1].x, v[k + 1].y);
+                            dst[7] = v[7];
                         }
                     }
                 }
