@@ -8,15 +8,20 @@
 // 0-8, mgt_group bits 9-10, mgt_channel bits 11-15), 256 sample bytes (byte
 // 64 f2 + k: fine channel 128 mgt_channel + 16 mgt_id + 4 mgt_group + f2,
 // input 64 pfb_id + k), and the XOR of the 128 data words; 16-bit words most
-// significant byte first.  One warp takes one packet: each lane realigns two
-// 32-bit words of samples (they start at byte 6), the warp XOR-reduces them
-// against the checksum, lane 0 decodes and checks the header and counters,
-// and the lanes store the samples as four 64-byte runs.  Slots (frame, group
-// of four channels, PFB) no good packet filled are then written with 0x88,
-// the appendix's invalid code, which CORR_ZERO_INVALID turns into zeros.
-// A slot is marked filled with a plain store (no value comes back, so the warp
-// never waits on it), and the repeats are counted at the end as good packets
-// minus distinct filled slots.
+// significant byte first.  Eight lanes take one packet (four packets per
+// warp): lane j owns data words 8 j .. 8 j + 7, i.e. 32 sample bytes of one
+// channel, loads the nine packet words that hold them (8-byte loads when the
+// stream is 8-byte aligned, issued one packet ahead), realigns them (the data
+// start at byte 6), XOR-reduces over the packet's lanes against the checksum,
+// decodes the header from the words its neighbours hold, and stores its bytes
+// with two 16-byte stores.  Sharing a warp among four packets divides the
+// header decode and the reduction, which bound the one-packet-per-warp form.
+// A slot is marked filled with a plain store (no value comes back, so no lane
+// waits on it).  A second pass, one thread per slot (frame, group of four
+// channels, PFB), writes the slots no good packet filled with 0x88, the
+// appendix's invalid code (CORR_ZERO_INVALID turns it into zeros), and counts
+// them; the repeats are the good packets minus the distinct filled slots,
+// added up in the same pass.
 #include "internal.cuh"
 
 namespace corr {
@@ -32,98 +37,148 @@ __device__ __forceinline__ unsigned be16(uint32_t w, int byte)   // big-endian 1
     return ((w >> (8 * byte)) & 0xFFu) << 8 | ((w >> (8 * byte + 8)) & 0xFFu);
 }
 
+// The packet words lane j of a packet needs: W j .. W j + W + 1 (W = 64 / L).
+template <int L, bool kAligned8>
+struct PacketWords {
+    static constexpr int W = 64 / L;
+    uint32_t v[2 * (W / 2 + 1)];
+    __device__ __forceinline__ void load(const uint32_t *w, int j)
+    {
+        if (kAligned8) {
+            // words W j .. W j + W + 1 (word 0 of the packet is lane 0's first)
+#pragma unroll
+            for (int k = 0; k <= W / 2; ++k) {
+                const uint2 u = __ldg(reinterpret_cast<const uint2 *>(w + W * j) + k);
+                v[2 * k] = u.x;
+                v[2 * k + 1] = u.y;
+            }
+        } else {
+#pragma unroll
+            for (int k = 0; k < W + 2; ++k) v[k] = __ldg(w + W * j + k);
+        }
+    }
+    // packet word W j + k
+    __device__ __forceinline__ uint32_t word(int k) const { return v[k]; }
+};
+
+template <int L, bool kAligned8>
 __global__ void __launch_bounds__(kIngestThreads)
 ingest_kernel(const uint32_t *__restrict__ pk, long long n_packets, int bank, uint8_t *__restrict__ volt,
               uint32_t *__restrict__ seen, int *__restrict__ counters)
 {
-    const int lane = threadIdx.x & 31;
+    constexpr int P = 32 / L, W = 64 / L;
+    const int lane = threadIdx.x & 31, sub = lane / L, j = lane % L;
     const long long warps = (long long)gridDim.x * (kIngestThreads / 32);
-    // per-warp counts (lane 0), added to the block's and then once to the
-    // global counters: one address hit by every packet would serialise
     __shared__ int block_counts[CORR_PKT_COUNTERS];
     if (threadIdx.x < CORR_PKT_COUNTERS) block_counts[threadIdx.x] = 0;
     __syncthreads();
     int mine[5] = {0, 0, 0, 0, 0};
-    for (long long q = blockIdx.x * (long long)(kIngestThreads / 32) + (threadIdx.x >> 5); q < n_packets;
-         q += warps) {
-        const uint32_t *w = pk + q * kWords;
-        // data word l: packet bytes 6 + 4l .. 9 + 4l, from 32-bit words 1 + l and 2 + l
-        const uint32_t d0 = __byte_perm(__ldg(w + 1 + lane), __ldg(w + 2 + lane), 0x5432);
-        const uint32_t d1 = __byte_perm(__ldg(w + 33 + lane), __ldg(w + 34 + lane), 0x5432);
-        uint32_t x = d0 ^ d1;
+    const long long step = warps * P;
+    long long q0 = (blockIdx.x * (long long)(kIngestThreads / 32) + (threadIdx.x >> 5)) * P;
+    PacketWords<L, kAligned8> cur;
+    if (q0 < n_packets) cur.load(pk + min(q0 + sub, n_packets - 1) * kWords, j);
+    // the loop runs for every lane of the warp (the shuffles below take all 32)
+    for (; q0 < n_packets; q0 += step) {
+        PacketWords<L, kAligned8> next;
+        if (q0 + step < n_packets) next.load(pk + min(q0 + step + sub, n_packets - 1) * kWords, j);
+        const long long q = q0 + sub;
+        const bool valid = q < n_packets;
+        // data word W j + k: packet bytes 6 + 4 (W j + k) .., from words W j + k + 1 and W j + k + 2
+        uint32_t d[W];
+        uint32_t x = 0;
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) x ^= __shfl_xor_sync(0xFFFFFFFFu, x, o);
-        const uint32_t w0 = __ldg(w), w1 = __ldg(w + 1), w65 = __ldg(w + 65);
-        // even packet bytes are the words' high bytes: data bytes 0 and 2 of each group of four
-        const unsigned xhi = (x ^ (x >> 16)) & 0xFFu, xlo = ((x >> 8) ^ (x >> 24)) & 0xFFu;
-        const unsigned header = be16(w0, 0), word2 = be16(w0, 2), word3 = be16(w1, 0);
-        const unsigned ck_hi = (w65 >> 16) & 0xFFu, ck_lo = (w65 >> 24) & 0xFFu;
-        const int tick = int(word2 & 1u), pfb = int((word2 >> 4) & 3u), mgt = int((word2 >> 6) & 7u);
-        const int bnk = int((word2 >> 9) & 31u);
-        const int frame = int(word3 & 511u), grp = int((word3 >> 9) & 3u), chan = int((word3 >> 11) & 31u);
-        int code = CORR_PKT_GOOD;
-        if (header != 0x0800u) code = CORR_PKT_BAD_HEADER;
-        else if (xhi != ck_hi || xlo != ck_lo) code = CORR_PKT_BAD_CHECKSUM;
-        else if (bnk != bank || chan >= 24 || frame >= kFrames ||
-                 (tick && (bnk | chan | grp | frame) != 0))
-            code = CORR_PKT_BAD_FIELD;
-        if (code != CORR_PKT_GOOD) {
-            ++mine[code];
-            continue;
+        for (int k = 0; k < W; ++k) {
+            d[k] = __byte_perm(cur.word(k + 1), cur.word(k + 2), 0x5432);
+            x ^= d[k];
         }
-        const int cgroup = 32 * chan + 4 * mgt + grp;
-        const long long slot = ((long long)frame * kGroups + cgroup) * 4 + pfb;
-        if (lane == 0) seen[slot] = 1u;
-        ++mine[CORR_PKT_GOOD];
-        // data word l holds channel f2 = l / 16, inputs 64 pfb + 4 (l % 16) .. + 3
-        const long long base = ((long long)frame * kChannels + 4 * cgroup) * kInputs + 64 * pfb + 4 * (lane & 15);
-        uint32_t *o = reinterpret_cast<uint32_t *>(volt);
-        o[(base + (long long)(lane >> 4) * kInputs) >> 2] = d0;
-        o[(base + (long long)(2 + (lane >> 4)) * kInputs) >> 2] = d1;
+#pragma unroll
+        for (int o = L / 2; o > 0; o >>= 1) x ^= __shfl_xor_sync(0xFFFFFFFFu, x, o);
+        const uint32_t w0 = __shfl_sync(0xFFFFFFFFu, cur.word(0), sub * L);
+        const uint32_t w1 = __shfl_sync(0xFFFFFFFFu, cur.word(1), sub * L);
+        const uint32_t w65 = __shfl_sync(0xFFFFFFFFu, cur.word(W + 1), sub * L + L - 1);
+        if (valid) {
+            // even packet bytes are the words' high bytes: data bytes 0 and 2 of each group of four
+            const unsigned xhi = (x ^ (x >> 16)) & 0xFFu, xlo = ((x >> 8) ^ (x >> 24)) & 0xFFu;
+            const unsigned header = be16(w0, 0), word2 = be16(w0, 2), word3 = be16(w1, 0);
+            const unsigned ck_hi = (w65 >> 16) & 0xFFu, ck_lo = (w65 >> 24) & 0xFFu;
+            const int tick = int(word2 & 1u), pfb = int((word2 >> 4) & 3u), mgt = int((word2 >> 6) & 7u);
+            const int bnk = int((word2 >> 9) & 31u);
+            const int frame = int(word3 & 511u), grp = int((word3 >> 9) & 3u), chan = int((word3 >> 11) & 31u);
+            int code = CORR_PKT_GOOD;
+            if (header != 0x0800u) code = CORR_PKT_BAD_HEADER;
+            else if (xhi != ck_hi || xlo != ck_lo) code = CORR_PKT_BAD_CHECKSUM;
+            else if (bnk != bank || chan >= 24 || frame >= kFrames ||
+                     (tick && (bnk | chan | grp | frame) != 0))
+                code = CORR_PKT_BAD_FIELD;
+            if (j == 0) ++mine[code];
+            if (code == CORR_PKT_GOOD) {
+                const int cgroup = 32 * chan + 4 * mgt + grp;
+                const long long slot = ((long long)frame * kGroups + cgroup) * 4 + pfb;
+                if (j == 0) seen[slot] = 1u;
+                // data word l holds channel f2 = l / 16, inputs 64 pfb + 4 (l % 16) .. + 3
+                const int l0 = W * j;
+                uint4 *o = reinterpret_cast<uint4 *>(volt +
+                                                     ((long long)frame * kChannels + 4 * cgroup + l0 / 16) * kInputs +
+                                                     64 * pfb + 4 * (l0 % 16));
+#pragma unroll
+                for (int k = 0; k < W; k += 4) o[k / 4] = make_uint4(d[k], d[k + 1], d[k + 2], d[k + 3]);
+            }
+        }
+        cur = next;
     }
-    if (lane == 0)
+    if ((lane % L) == 0)
         for (int c = 0; c < 5; ++c)
             if (mine[c]) atomicAdd(block_counts + c, mine[c]);
     __syncthreads();
     if (threadIdx.x < 5 && block_counts[threadIdx.x]) atomicAdd(counters + threadIdx.x, block_counts[threadIdx.x]);
 }
 
-// One thread per (slot, channel f2): a slot nobody filled gets 64 bytes of 0x88.
+// One thread per slot (frame, group of four channels, PFB): a slot nobody
+// filled gets its four 64-byte runs of 0x88.
 __global__ void __launch_bounds__(kIngestThreads)
 ingest_missing_kernel(uint8_t *__restrict__ volt, const uint32_t *__restrict__ seen, int *__restrict__ counters)
 {
-    const long long n = (long long)CORR_PKT_SLOTS * 4;
     int missing = 0;
-    for (long long e = blockIdx.x * (long long)kIngestThreads + threadIdx.x; e < n;
-         e += (long long)gridDim.x * kIngestThreads) {
-        const long long slot = e >> 2;
+    for (long long slot = blockIdx.x * (long long)kIngestThreads + threadIdx.x; slot < CORR_PKT_SLOTS;
+         slot += (long long)gridDim.x * kIngestThreads) {
         if (seen[slot]) continue;
-        const int f2 = int(e & 3);
         const int pfb = int(slot & 3);
         const long long fg = slot >> 2;                 // frame * kGroups + cgroup
         const long long frame = fg / kGroups, cgroup = fg % kGroups;
-        uint4 *dst = reinterpret_cast<uint4 *>(volt + (frame * kChannels + 4 * cgroup + f2) * kInputs + 64 * pfb);
         const uint4 inv = make_uint4(0x88888888u, 0x88888888u, 0x88888888u, 0x88888888u);
-        dst[0] = inv;
-        dst[1] = inv;
-        dst[2] = inv;
-        dst[3] = inv;
-        if (f2 == 0) ++missing;
+#pragma unroll
+        for (int f2 = 0; f2 < 4; ++f2) {
+            uint4 *dst = reinterpret_cast<uint4 *>(volt + (frame * kChannels + 4 * cgroup + f2) * kInputs + 64 * pfb);
+            dst[0] = inv;
+            dst[1] = inv;
+            dst[2] = inv;
+            dst[3] = inv;
+        }
+        ++missing;
     }
     __shared__ int block_missing;
     if (threadIdx.x == 0) block_missing = 0;
     __syncthreads();
     if (missing) atomicAdd(&block_missing, missing);
     __syncthreads();
-    if (threadIdx.x == 0 && block_missing) atomicAdd(counters + CORR_PKT_MISSING, block_missing);
+    // repeats = good packets - distinct filled slots = GOOD - (SLOTS - MISSING):
+    // every block adds its missing slots to both counters, and block 0 adds
+    // GOOD - SLOTS (final: the ingest kernel ran before this one)
+    if (threadIdx.x == 0) {
+        int dup = block_missing;
+        if (blockIdx.x == 0) dup += counters[CORR_PKT_GOOD] - CORR_PKT_SLOTS;
+        if (block_missing) atomicAdd(counters + CORR_PKT_MISSING, block_missing);
+        if (dup) atomicAdd(counters + CORR_PKT_DUPLICATE, dup);
+    }
 }
 
-// Repeated packets: every good packet fills one slot, so the repeats are the
-// good packets beyond the distinct slots filled (all slots but the missing).
-__global__ void ingest_repeats_kernel(int *__restrict__ counters)
+// The slot marks (4-byte aligned) and the counters, zeroed in one launch.
+__global__ void __launch_bounds__(kIngestThreads)
+ingest_clear_kernel(uint32_t *__restrict__ seen, int *__restrict__ counters)
 {
-    counters[CORR_PKT_DUPLICATE] =
-        counters[CORR_PKT_GOOD] - (CORR_PKT_SLOTS - counters[CORR_PKT_MISSING]);
+    for (int e = blockIdx.x * kIngestThreads + threadIdx.x; e < CORR_PKT_SLOTS; e += gridDim.x * kIngestThreads)
+        seen[e] = 0u;
+    if (blockIdx.x == 0 && threadIdx.x < CORR_PKT_COUNTERS) counters[threadIdx.x] = 0;
 }
 
 }  // namespace
@@ -131,21 +186,29 @@ __global__ void ingest_repeats_kernel(int *__restrict__ counters)
 cudaError_t launch_ingest(const uint8_t *packets, long long n_packets, int bank, uint8_t *volt, void *seen,
                           int32_t *counters, cudaStream_t s)
 {
-    cudaError_t e = cudaMemsetAsync(seen, 0, size_t(CORR_PKT_SEEN_BYTES), s);
-    if (e == cudaSuccess) e = cudaMemsetAsync(counters, 0, sizeof(int32_t) * CORR_PKT_COUNTERS, s);
+    ingest_clear_kernel<<<(CORR_PKT_SLOTS + kIngestThreads - 1) / kIngestThreads, kIngestThreads, 0, s>>>(
+        static_cast<uint32_t *>(seen), counters);
+    cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
     if (n_packets > 0) {
-        const long long blocks = (n_packets + kIngestThreads / 32 - 1) / (kIngestThreads / 32);
-        ingest_kernel<<<unsigned(blocks < 152 * 64 ? blocks : 152 * 64), kIngestThreads, 0, s>>>(
-            reinterpret_cast<const uint32_t *>(packets), n_packets, bank, volt, static_cast<uint32_t *>(seen),
-            counters);
+        constexpr int kL = 8;       // lanes per packet (8 measured faster than 4 and 16)
+        const long long per_block = (kIngestThreads / 32) * (32 / kL);
+        const long long blocks = (n_packets + per_block - 1) / per_block;
+        const unsigned grid = unsigned(blocks < 152 * 64 ? blocks : 152 * 64);
+        const uint32_t *p32 = reinterpret_cast<const uint32_t *>(packets);
+        if ((reinterpret_cast<uintptr_t>(packets) & 7) == 0)
+            ingest_kernel<kL, true><<<grid, kIngestThreads, 0, s>>>(p32, n_packets, bank, volt,
+                                                                     static_cast<uint32_t *>(seen), counters);
+        else
+            ingest_kernel<kL, false><<<grid, kIngestThreads, 0, s>>>(p32, n_packets, bank, volt,
+                                                                      static_cast<uint32_t *>(seen), counters);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    ingest_missing_kernel<<<152 * 32, kIngestThreads, 0, s>>>(volt, static_cast<const uint32_t *>(seen), counters);
+    ingest_missing_kernel<<<(CORR_PKT_SLOTS + kIngestThreads - 1) / kIngestThreads, kIngestThreads, 0, s>>>(
+        volt, static_cast<const uint32_t *>(seen), counters);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
-    ingest_repeats_kernel<<<1, 1, 0, s>>>(counters);
     return cudaGetLastError();
 }
 

@@ -57,9 +57,10 @@
 //   warps 18-21 epilogue: TMEM -> int32, corrections, packed-triangle store
 //              (fp32 on exact integers; each store instruction writes 32
 //              consecutive elements of one packed row)
-//   warps 23-24 (launches that also form the incoherent beam only): the
+//   warps 23-26 (launches that also form the incoherent beam only): the
 //              total power of each tile's inputs per sample, read from the
-//              packed bytes in shared memory and added into the beam
+//              packed bytes in shared memory and added into the beam (warps
+//              23-24 the B tile's rows, 25-26 the A tile's)
 // TMEM holds two accumulators (2 x 256 columns).  A single item takes the
 // next one in turn, so its epilogue overlaps the main loop of the next item; a
 // pair item takes both, its diagonal part in the one that is released first.
@@ -103,11 +104,11 @@ constexpr int kTeams = 2, kTeamWarps = kConvWarps / kTeams;   // converter teams
 static_assert(kPackedStages % kTeams == 0, "packed slots must be team-exclusive");
 constexpr int kThreads = (2 + kConvWarps + kEpiWarps + 1) * 32;   // 736: warp 22 converts, warp 17 idles
 constexpr int kFirstConvWarp = 2, kFirstEpiWarp = 2 + kConvWarps;
-// With the incoherent beam, warps 23 and 24 form it from the packed bytes in
-// shared memory (32 rows of each stage each); the registers (80 a thread)
-// leave room for exactly these two more warps.
-constexpr int kBeamWarps = 2, kFirstBeamWarp = kThreads / 32;
-constexpr int kThreadsBeam = kThreads + kBeamWarps * 32;   // 800
+// With the incoherent beam, warps 23-26 form it from the packed bytes in
+// shared memory (32 rows of one tile of each stage each); at 72 registers a
+// thread the launch's 864 threads fit the register file.
+constexpr int kBeamWarps = 4, kFirstBeamWarp = kThreads / 32;
+constexpr int kThreadsBeam = kThreads + kBeamWarps * 32;   // 864
 constexpr int kTmemCols = 512;               // 2 accumulator slots x (128 Re + 128 Im)
 // A pair item needs both TMEM accumulators free before its first MMA, so the
 // previous item's epilogue is exposed once per pair.  On short launches that
@@ -311,16 +312,6 @@ __device__ __forceinline__ void mma_commit(uint32_t bar)
 
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
-
-__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16])
-{
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];\n"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
-          "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-}
 
 __device__ __forceinline__ void tmem_ld8(uint32_t taddr, uint32_t (&r)[8])
 {
@@ -649,7 +640,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
         // The B tile (upper half of the packed stage) becomes the planes M, R and
         // -M, the A tile (lower half) R and M; a diagonal item's single tile is
         // both, as B.
-        const int ci = warp <= 16 ? warp - 2 : 15;
+        const int ci = warp <= 16 ? warp - kFirstConvWarp : 15;
         const int team = ci / kTeamWarps;
         const int u = (ci % kTeamWarps) * 32 + lane;   // 0..255
         const int c = u & 7, q = u >> 3;                                         // q 0..31
@@ -777,13 +768,15 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
         // Every tile's 128 inputs are added once per channel and sample: the
         // B tile of each diagonal item (single items) or pair item, and for the
         // pair item (1, 0) its A tile (0) too, which the diagonal item (0, 0)
-        // then leaves out.  Lane l owns row 32 w + l of each stage (a sample)
-        // and reads its 8 chunks rotated by l, so the 8 lanes of a quarter-warp
+        // then leaves out.  Beam warp w takes tile B (w < 2) or A (w >= 2);
+        // its lane l owns row 32 (w mod 2) + l of each stage (a sample) and
+        // reads its 8 chunks rotated by l, so the 8 lanes of a quarter-warp
         // always hit 8 different 16-byte bank groups.  The warps walk every
         // stage of the CTA in order and release each packed slot with the
         // converters.
         const int bw = warp - kFirstBeamWarp;
-        const int row = bw * 32 + lane;
+        const int row = (bw & 1) * 32 + lane;
+        const bool upper = bw < 2;                      // the B tile, in the upper half of the packed stage
         uint32_t g0 = 0;
         bool ok = true;
         for (int item = first_item; ok && item < p.n_items; item += item_step) {
@@ -806,23 +799,19 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 }
                 (void)mbar_try(bar_packed_full(pstage), pphase);   // completed: acquire for every lane
                 const int t = int(gg - g0) * kTc + row;
-                if ((b_tile || a_tile) && t < A.nt) {
-                    const uint8_t *pk = smem + kSmPacked + pstage * kPackedStageBytes + row * 128;
+                if ((upper ? b_tile : a_tile) && t < A.nt) {
+                    const uint8_t *src = smem + kSmPacked + pstage * kPackedStageBytes + row * 128 +
+                                         (upper ? kPackedTileBytes : 0);
                     // four independent sums (one per word of a chunk) keep the
                     // dp4a chains short
                     int a0 = 0, a1 = 0, a2 = 0, a3 = 0;
 #pragma unroll
-                    for (int half = 0; half < 2; ++half) {
-                        if (half == 0 ? !b_tile : !a_tile) continue;
-                        const uint8_t *src = pk + (half == 0 ? kPackedTileBytes : 0);
-#pragma unroll
-                        for (int k = 0; k < 8; ++k) {
-                            const uint4 w = *reinterpret_cast<const uint4 *>(src + ((k + lane) & 7) * 16);
-                            a0 = power256(w.x, kZeroInvalid, a0);
-                            a1 = power256(w.y, kZeroInvalid, a1);
-                            a2 = power256(w.z, kZeroInvalid, a2);
-                            a3 = power256(w.w, kZeroInvalid, a3);
-                        }
+                    for (int k = 0; k < 8; ++k) {
+                        const uint4 w = *reinterpret_cast<const uint4 *>(src + ((k + lane) & 7) * 16);
+                        a0 = power256(w.x, kZeroInvalid, a0);
+                        a1 = power256(w.y, kZeroInvalid, a1);
+                        a2 = power256(w.z, kZeroInvalid, a2);
+                        a3 = power256(w.w, kZeroInvalid, a3);
                     }
                     atomicAdd(beam_f + (size_t)((A.beam_t0 + t) / A.beam_avg) * A.n_chan, (a0 + a1 + a2 + a3) >> 8);
                 }

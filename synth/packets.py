@@ -82,3 +82,15 @@ def packetise(block: np.ndarray, bank: int = 0) -> np.ndarray:
     order pfb_id 0..3, mgt_id 0..7."""
     return np.concatenate([lane_packets(block, p, m, bank) for p in range(PFBS)
                            for m in range(LANES_PER_PFB)])
+
+
+def arrival_order(block: np.ndarray, bank: int = 0) -> np.ndarray:
+    """The same packets in the order a receiver collects them (Sections 3.3.3
+    and 3.4.1: each lane's packets travel in time-contiguous blocks of 2000,
+    one coarse channel's four groups x 500 frames, one connection per lane,
+    and each block is placed as it arrives): the 32 lanes' blocks of coarse
+    channel 0, then of coarse channel 1, and so on, lanes in order pfb_id
+    0..3, mgt_id 0..7.  uint8 [32 * 48000][264]."""
+    per_block = GROUPS * FRAMES
+    lanes = [lane_packets(block, p, m, bank) for p in range(PFBS) for m in range(LANES_PER_PFB)]
+    return np.concatenate([lane[c * per_block:(c + 1) * per_block] for c in range(COARSE) for lane in lanes])

@@ -64,6 +64,17 @@ def test_whole_bank_round_trip_into_xengine():
     assert np.array_equal(got, oracle.to_int32(oracle.xmac(block[:, [0, 2047]])))
 
 
+def test_whole_bank_in_arrival_order():
+    """The order a receiver collects the lanes' 2000-packet blocks in (the
+    benchmark's order) gives the same block and no rejections."""
+    block = np.random.default_rng(8).integers(0, 256, (500, 3072, 256), dtype=np.uint8)
+    stream = pkts.arrival_order(block, 3)
+    volt_t, cnt = corr.ingest_packets(torch.from_numpy(stream).cuda(), 3)
+    torch.cuda.synchronize()
+    assert cnt.cpu().tolist() == [len(stream), 0, 0, 0, 0, 0]
+    assert torch.equal(volt_t.cpu(), torch.from_numpy(block))
+
+
 def test_missing_packets_are_invalid_samples():
     """A lane that sent nothing leaves invalid samples, which the zero-invalid
     reading turns into zeros: the correlation equals that of the zeroed block."""
