@@ -47,6 +47,8 @@
 // Pipeline (persistent, one CTA per SM, work item = (channel, I tile, J tile)):
 //   warp 0     TMA producer: packed bytes [64 samples][128 inputs] per tile,
 //              with L2 prefetch of the tiles kPrefetchStages stages ahead
+//              (across item boundaries: an item's last stages prefetch the
+//              CTA's next item's first)
 //   warp 1     TMEM allocator and single-thread MMA issuer
 //   warps 2-16, 22  converters: packed bytes -> E4M3 planes (+ per-input
 //              sums), as two teams of 8 warps that take alternate 64-sample
@@ -502,14 +504,31 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 const CUtensorMap *tmap = &tmaps.m[it.a];
                 const int f = it.f, I = it.I, J = it.J;
                 const bool diag = it.diag;
-                for (int s = 0; s < kPrefetchStages && s < n_stages; ++s) {
-                    tma_prefetch_3d(tmap, I * kTile, f, s * kTc);
-                    if (!diag) tma_prefetch_3d(tmap, J * kTile, f, s * kTc);
+                // the item's first stages were prefetched during the previous
+                // item (the first item's here); its later ones run ahead below,
+                // and its last ones prefetch the next item's first
+                if (item == first_item)
+                    for (int s = 0; s < kPrefetchStages && s < n_stages; ++s) {
+                        tma_prefetch_3d(tmap, I * kTile, f, s * kTc);
+                        if (!diag) tma_prefetch_3d(tmap, J * kTile, f, s * kTc);
+                    }
+                const int nitem = item + item_step;
+                Item nit{};
+                int n_nst = 0;
+                const CUtensorMap *ntmap = nullptr;
+                if (nitem < p.n_items) {
+                    nit = decode_item(p, nitem);
+                    n_nst = p.a[nit.a].n_stages;
+                    ntmap = &tmaps.m[nit.a];
                 }
                 for (int s = 0; s < n_stages; ++s) {
                     if (s + kPrefetchStages < n_stages) {
                         tma_prefetch_3d(tmap, I * kTile, f, (s + kPrefetchStages) * kTc);
                         if (!diag) tma_prefetch_3d(tmap, J * kTile, f, (s + kPrefetchStages) * kTc);
+                    } else if (s + kPrefetchStages - n_stages < n_nst) {
+                        const int ns = s + kPrefetchStages - n_stages;
+                        tma_prefetch_3d(ntmap, nit.I * kTile, nit.f, ns * kTc);
+                        if (!nit.diag) tma_prefetch_3d(ntmap, nit.J * kTile, nit.f, ns * kTc);
                     }
                     if (!mbar_wait(bar_packed_empty(stage), phase ^ 1u, abort, p.status, 1, p.wait_limit)) {
                         ok = false;
