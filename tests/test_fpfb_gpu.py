@@ -62,8 +62,9 @@ def _check_codes(got, want_spec, bound, scale):
         assert np.mean(g == want) > 0.99
 
 
-@pytest.mark.parametrize("Q,N,M", [(2, 20, 130), (1, 8, 1), (3, 64, 240)],
-                         ids=["ragged_inputs_and_frames", "one_frame", "three_coarse"])
+@pytest.mark.parametrize("Q,N,M", [(2, 20, 130), (1, 8, 1), (3, 64, 240), (1, 1, 9), (2, 17, 16)],
+                         ids=["ragged_inputs_and_frames", "one_frame", "three_coarse", "one_input",
+                              "odd_inputs"])
 def test_fine_pfb_12_taps(Q, N, M):
     taps = 12
     S = 128 * (M + taps - 1)
