@@ -47,6 +47,9 @@ WORKLOADS = {
     "coarse_channel": ([(256, 128, 5000)], 1, 1502),
     # one integration of the full band (3.9 GB of voltages): a small case for traffic captures
     "integration": ([(256, 3072, 5000)], 1, 1503),
+    # a quarter of the band, one integration (1 GB of voltages, 1536 items: about ten per CTA, so
+    # the steady state rather than the tail): a small case for full profiles
+    "quarter_band": ([(256, 768, 5000)], 1, 1507),
     "uneven_batch": ([(128, 1536, 2000), (256, 3072, 5000), (1024, 512, 10000)], 1, 1504),
     # one 50 ms bank of the full band (the packet ingest's unit): a small case for profiles
     "bank": ([(256, 3072, 500)], 1, 1506),
