@@ -903,8 +903,11 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                     DaA = SmA - SrA;
                     named_sync(2, kEpiWarps * 32);
                     // input b's column terms, as floats in column order (the B sums
-                    // area holds exactly 128 float2): -8 E_b for Re, -8 D_b for Im
-                    reinterpret_cast<float2 *>(sbB)[il] = make_float2(float(-8 * EaB), float(-8 * DaB));
+                    // area holds exactly 2 x 128 floats): -8 E_b for Re in the first
+                    // half, -8 D_b for Im in the second, so that two adjacent columns'
+                    // terms are one float pair for the paired arithmetic below
+                    reinterpret_cast<float *>(sbB)[il] = float(-8 * EaB);
+                    reinterpret_cast<float *>(sbB)[kTile + il] = float(-8 * DaB);
                 }
                 named_sync(2, kEpiWarps * 32);
                 if (!ok) break;
@@ -920,7 +923,8 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                 // 2^22) as the low bits of the float's encoding
                 const float row_re = float(128 * T_eff - 8 * Ea) + 12582912.0f;
                 const float row_im = float(8 * Da) + 12582912.0f;
-                const float4 *col = reinterpret_cast<const float4 *>(sbB);
+                const float4 *colre = reinterpret_cast<const float4 *>(sbB);          // -8 E_b, b = 4 m .. 4 m + 3
+                const float4 *colim = reinterpret_cast<const float4 *>(sbB + kTile);  // -8 D_b
                 const uint32_t taddr = tmem + uint32_t(sl * 256) + (uint32_t(q * 32) << 16);
                 const int i0 = it.I * kTile;
                 // in the diagonal part, column b holds output row i0 + b, whose
@@ -948,14 +952,26 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                     for (int k = 0; k < 8; ++k) v[k] = make_int2(0, 0);
                     tmem_wait_ld();
 #pragma unroll
-                    for (int k = 0; k < 8; k += 2) {
-                        const float4 c = col[(c0 + k) >> 1];
-                        v[k].x += __float_as_int(fmaf(__uint_as_float(vre[k]), 262144.0f, c.x) + row_re) - 0x4B400000;
-                        v[k].y += __float_as_int(fmaf(__uint_as_float(vim[k]), -262144.0f, c.y) + row_im) - 0x4B400000;
-                        v[k + 1].x +=
-                            __float_as_int(fmaf(__uint_as_float(vre[k + 1]), 262144.0f, c.z) + row_re) - 0x4B400000;
-                        v[k + 1].y +=
-                            __float_as_int(fmaf(__uint_as_float(vim[k + 1]), -262144.0f, c.w) + row_im) - 0x4B400000;
+                    for (int k = 0; k < 8; k += 4) {
+                        // paired fp32 (sm_100+): each instruction does two columns
+                        const float4 cr = colre[(c0 + k) >> 2], ci = colim[(c0 + k) >> 2];
+#pragma unroll
+                        for (int e = 0; e < 4; e += 2) {
+                            const float2 re = __fadd2_rn(
+                                __ffma2_rn(make_float2(__uint_as_float(vre[k + e]), __uint_as_float(vre[k + e + 1])),
+                                           make_float2(262144.0f, 262144.0f),
+                                           e == 0 ? make_float2(cr.x, cr.y) : make_float2(cr.z, cr.w)),
+                                make_float2(row_re, row_re));
+                            const float2 im = __fadd2_rn(
+                                __ffma2_rn(make_float2(__uint_as_float(vim[k + e]), __uint_as_float(vim[k + e + 1])),
+                                           make_float2(-262144.0f, -262144.0f),
+                                           e == 0 ? make_float2(ci.x, ci.y) : make_float2(ci.z, ci.w)),
+                                make_float2(row_im, row_im));
+                            v[k + e].x += __float_as_int(re.x) - 0x4B400000;
+                            v[k + e + 1].x += __float_as_int(re.y) - 0x4B400000;
+                            v[k + e].y += __float_as_int(im.x) - 0x4B400000;
+                            v[k + e + 1].y += __float_as_int(im.y) - 0x4B400000;
+                        }
                     }
                     int2 *pk = p0;
                     if (!fresh) {
@@ -1003,14 +1019,25 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                         tmem_wait_ld();
                         int2 v[8];
 #pragma unroll
-                        for (int k = 0; k < 8; k += 2) {
-                            const float4 c = col[(c0 + k) >> 1];
-                            v[k].x = __float_as_int(fmaf(__uint_as_float(vre[k]), 262144.0f, c.x) + row_re) - 0x4B400000;
-                            v[k].y = __float_as_int(fmaf(__uint_as_float(vim[k]), 262144.0f, -c.y) + rrow_im) - 0x4B400000;
-                            v[k + 1].x =
-                                __float_as_int(fmaf(__uint_as_float(vre[k + 1]), 262144.0f, c.z) + row_re) - 0x4B400000;
-                            v[k + 1].y =
-                                __float_as_int(fmaf(__uint_as_float(vim[k + 1]), 262144.0f, -c.w) + rrow_im) - 0x4B400000;
+                        for (int k = 0; k < 8; k += 4) {
+                            const float4 cr = colre[(c0 + k) >> 2], ci = colim[(c0 + k) >> 2];
+#pragma unroll
+                            for (int e = 0; e < 4; e += 2) {
+                                const float2 re = __fadd2_rn(
+                                    __ffma2_rn(make_float2(__uint_as_float(vre[k + e]), __uint_as_float(vre[k + e + 1])),
+                                               make_float2(262144.0f, 262144.0f),
+                                               e == 0 ? make_float2(cr.x, cr.y) : make_float2(cr.z, cr.w)),
+                                    make_float2(row_re, row_re));
+                                const float2 im = __fadd2_rn(
+                                    __ffma2_rn(make_float2(__uint_as_float(vim[k + e]), __uint_as_float(vim[k + e + 1])),
+                                               make_float2(262144.0f, 262144.0f),
+                                               e == 0 ? make_float2(-ci.x, -ci.y) : make_float2(-ci.z, -ci.w)),
+                                    make_float2(rrow_im, rrow_im));
+                                v[k + e].x = __float_as_int(re.x) - 0x4B400000;
+                                v[k + e + 1].x = __float_as_int(re.y) - 0x4B400000;
+                                v[k + e].y = __float_as_int(im.x) - 0x4B400000;
+                                v[k + e + 1].y = __float_as_int(im.y) - 0x4B400000;
+                            }
                         }
                         int2 *const dst = rowp + c0;
                         if (!live) {
