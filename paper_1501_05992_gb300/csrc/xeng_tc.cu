@@ -144,7 +144,8 @@ struct ArrayParams {
     int fresh;
     int pairs;      // pair items in use (else one item per tile pair)
     int rot_step;   // item rotation per stride round (see decode_item)
-    int32_t *beam;  // incoherent beam [.][n_chan], added to (NULL: none)
+    int32_t *beam;  // incoherent beam [.][beam_ld], added to (NULL: none)
+    int beam_ld;    // channels of a beam row
     int beam_avg, beam_t0;   // samples per beam value; the launch's first sample
 };
 
@@ -343,7 +344,7 @@ __host__ __device__ __forceinline__ int items_per_channel(int n_tiles, bool pair
     return n_tiles * (n_tiles + 1) / 2 - (pairs ? n_tiles - 1 : 0);
 }
 
-__device__ __forceinline__ void item_tiles(int k, int n_tiles, bool pairs, int &I, int &J, int &kind)
+__host__ __device__ __forceinline__ void item_tiles(int k, int n_tiles, bool pairs, int &I, int &J, int &kind)
 {
     if (!pairs) {
         // one item per tile pair, numbered row by row of the tile triangle
@@ -832,7 +833,7 @@ xeng_tc_kernel(const __grid_constant__ Tmaps tmaps, const __grid_constant__ Para
                         a2 = power256(w.z, kZeroInvalid, a2);
                         a3 = power256(w.w, kZeroInvalid, a3);
                     }
-                    atomicAdd(beam_f + (size_t)((A.beam_t0 + t) / A.beam_avg) * A.n_chan, (a0 + a1 + a2 + a3) >> 8);
+                    atomicAdd(beam_f + (size_t)((A.beam_t0 + t) / A.beam_avg) * A.beam_ld, (a0 + a1 + a2 + a3) >> 8);
                 }
                 __syncwarp();
                 if (lane == 0) mbar_arrive(bar_packed_empty(pstage));
@@ -1161,6 +1162,43 @@ cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus 
     return cudaSuccess;
 }
 
+// Channels [c0, c0 + chans) of one array, as one array of the launch.
+struct Span {
+    const TcArray *A;
+    int c0, chans;
+    bool pairs;
+};
+
+// Largest cost over the CTAs of the static schedule (CTA c takes items c, c +
+// grid, ...), in half tile pairs of MMA work, with conversion counted in: a pair
+// item (two tile pairs, two tiles converted) 4, an off-diagonal item (one tile
+// pair, two tiles converted) 3, a diagonal item (one tile pair, one tile) 2.
+long long schedule_max_cost(const Span *sp, int m, int grid)
+{
+    static thread_local long long cost[1024];
+    const int g = grid < 1024 ? grid : 1024;
+    for (int c = 0; c < g; ++c) cost[c] = 0;
+    long long item = 0;
+    for (int k = 0; k < m; ++k) {
+        const int n_tiles = (sp[k].A->n + kTile - 1) / kTile;
+        const bool pairs = sp[k].pairs;
+        const int per_chan = items_per_channel(n_tiles, pairs);
+        const bool rot = grid % per_chan == 0;
+        const long long begin = item;
+        for (long long local = 0; local < (long long)sp[k].chans * per_chan; ++local, ++item) {
+            const long long f = local / per_chan;
+            const int kk = int(local - f * per_chan);
+            const long long round = (begin + f * per_chan) / grid;
+            int I, J, kind;
+            item_tiles(rot ? int((kk + round) % per_chan) : kk, n_tiles, pairs, I, J, kind);
+            cost[item % g] += kind == kPairItem ? 4 : kind == kOffItem ? 3 : 2;
+        }
+    }
+    long long mx = 0;
+    for (int c = 0; c < g; ++c) mx = cost[c] > mx ? cost[c] : mx;
+    return mx;
+}
+
 cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, int dev,
                          DeviceStatus *status, const TcOptions &opt, cudaStream_t s)
 {
@@ -1175,39 +1213,97 @@ cudaError_t launch_group(const TcArray *arrays, int count, bool zero_invalid, in
             order[y] = order[y - 1];
             order[y - 1] = t;
         }
-    Tmaps maps;
-    Params prm{};
+    Span sp[kMaxArrays];
     long long items = 0;
     for (int k = 0; k < m; ++k) {
         const TcArray &A = arrays[order[k]];
+        const int n_tiles = (A.n + kTile - 1) / kTile;
+        const int n_stages = (A.nt + kTc - 1) / kTc;
+        const bool want_pairs = A.items == TcItems::kPairs ||
+                                (A.items == TcItems::kAuto && n_stages >= kPairMinStages);
+        sp[k] = Span{&A, 0, A.n_chan, n_tiles > 1 && want_pairs};
+        items += (long long)A.n_chan * items_per_channel(n_tiles, sp[k].pairs);
+    }
+    // The last round of the static schedule: where the last array runs pair
+    // items, its last x channels may run as single items instead, x the fewest
+    // channels that fill the last (partial) round with single items, so that a
+    // CTA's extra item is one tile pair, not two; taken when it lowers the
+    // largest cost of a CTA (for 256 inputs x 3072 channels on 152 SMs, x = 32:
+    // 96 single items instead of 32 pair and 32 diagonal items).  Either
+    // schedule computes the same sums: only the time differs.
+    const int sms = g_sm_count[dev];
+    if (sp[m - 1].pairs && m < kMaxArrays && items > sms && items <= (1 << 22)) {
+        const Span last = sp[m - 1];
+        const int n_tiles = (last.A->n + kTile - 1) / kTile;
+        const int pp = items_per_channel(n_tiles, true), ps = items_per_channel(n_tiles, false);
+        int x = 1;
+        for (; x < last.chans; ++x) {
+            const long long n2 = items + (long long)x * (ps - pp);
+            const long long r = n2 % sms;
+            if ((r ? r : sms) <= (long long)x * ps) break;
+        }
+        if (x < last.chans) {
+            // the decision depends on the launch's shapes only: keep the last one
+            struct Key {
+                long long items;
+                int sms, m, n, chans;
+                bool take;
+            };
+            static thread_local Key memo{-1, 0, 0, 0, 0, false};
+            const bool hit = memo.items == items && memo.sms == sms && memo.m == m && memo.n == last.A->n &&
+                             memo.chans == last.chans;
+            bool take = memo.take;
+            sp[m - 1].chans = last.chans - x;
+            sp[m] = Span{last.A, last.chans - x, x, false};
+            if (!hit) {
+                sp[m - 1] = last;
+                const long long before = schedule_max_cost(sp, m, sms);
+                sp[m - 1].chans = last.chans - x;
+                take = schedule_max_cost(sp, m + 1, sms) < before;
+                memo = Key{items, sms, m, last.A->n, last.chans, take};
+            }
+            if (take) {
+                ++m;
+                items += (long long)x * (ps - pp);
+            } else {
+                sp[m - 1] = last;
+            }
+        }
+    }
+    Tmaps maps;
+    Params prm{};
+    items = 0;
+    for (int k = 0; k < m; ++k) {
+        const TcArray &A = *sp[k].A;
+        const int c0 = sp[k].c0;
         // extent n along the inputs: a box reaching past it (a ragged last tile)
         // reads zero bytes, i.e. samples 0 + 0i, which cancel in the corrections
         const cuuint64_t ld = cuuint64_t(A.ld ? A.ld : A.n);
-        const cuuint64_t dims[3] = {cuuint64_t(A.n), cuuint64_t(A.n_chan), cuuint64_t(A.nt)};
+        const cuuint64_t dims[3] = {cuuint64_t(A.n), cuuint64_t(sp[k].chans), cuuint64_t(A.nt)};
         const cuuint64_t strides[2] = {ld, ld * cuuint64_t(A.n_chan)};
         const cuuint32_t box[3] = {cuuint32_t(kTile), 1u, cuuint32_t(kTc)};
         const cuuint32_t estr[3] = {1u, 1u, 1u};
-        CUresult cr = enc(&maps.m[k], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3, const_cast<uint8_t *>(A.volt), dims,
-                          strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
+        CUresult cr = enc(&maps.m[k], CU_TENSOR_MAP_DATA_TYPE_UINT8, 3,
+                          const_cast<uint8_t *>(A.volt) + size_t(c0) * ld, dims, strides, box, estr,
+                          CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE,
                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
         if (cr != CUDA_SUCCESS) return cudaErrorInvalidValue;
         ArrayParams &P = prm.a[k];
-        P.acc = A.acc;
+        P.acc = A.acc + size_t(c0) * size_t(n_pairs(A.n)) * 2;
         P.n = A.n;
-        P.n_chan = A.n_chan;
+        P.n_chan = sp[k].chans;
         P.nt = A.nt;
         P.n_tiles = (A.n + kTile - 1) / kTile;
         P.n_stages = (A.nt + kTc - 1) / kTc;
         P.item_begin = int(items);
         P.fresh = A.fresh ? 1 : 0;
-        const bool want_pairs = A.items == TcItems::kPairs ||
-                                (A.items == TcItems::kAuto && P.n_stages >= kPairMinStages);
-        P.pairs = P.n_tiles > 1 && want_pairs ? 1 : 0;
+        P.pairs = sp[k].pairs ? 1 : 0;
         P.per_chan = items_per_channel(P.n_tiles, P.pairs != 0);
-        P.beam = A.beam;
+        P.beam = A.beam ? A.beam + c0 : nullptr;
+        P.beam_ld = A.n_chan;
         P.beam_avg = A.beam_avg > 0 ? A.beam_avg : 1;
         P.beam_t0 = A.beam_t0;
-        items += (long long)A.n_chan * P.per_chan;
+        items += (long long)sp[k].chans * P.per_chan;
     }
     if (items > 0x7FFFFFFF) return cudaErrorInvalidValue;
     prm.n_arrays = m;

@@ -259,3 +259,32 @@ def test_batch_with_padded_tensor_core_arrays():
     for v, o in zip(volts, outs):
         assert np.array_equal(o.cpu().numpy(), oracle.to_int32(oracle.xmac(v)))
     b.close()
+
+
+def test_tc_last_round_split_exact():
+    """Launches whose item count leaves a partial last round on the GPU's SMs,
+    where the last channels run as single items instead of pair items (200
+    inputs on a padded copy, 384 inputs with three tiles): whole triangles of
+    the first, the last paired and the single-item channels, fresh and
+    accumulating launches (the same samples twice), and the fused beam of
+    every channel."""
+    if not path_available("tc_fp8", 128):
+        pytest.skip("tc_fp8 unsupported")
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    # pair items from 64 stages on: 4100 samples; 2 and 4 items per channel
+    for N, F in [(200, sms + 8), (384, sms // 4 + 6)]:
+        T = 4100
+        volt = _rand((T, F, N), N + F)
+        c = corr.Correlator(N, F, 2 * T, path="tc_fp8")
+        d = torch.from_numpy(volt).cuda()
+        tri, beam = c.integrate_beam(d, 4)
+        c.accumulate(d)
+        c.accumulate(d)
+        acc = c.dump()
+        c.sync()
+        c.close()
+        chans = sorted({0, F - 25, F - 9, F - 8, F - 7, F - 1})
+        vis = oracle.xmac(volt[:, chans])
+        assert np.array_equal(tri[chans].cpu().numpy(), oracle.to_int32(vis)), (N, F)
+        assert np.array_equal(acc[chans].cpu().numpy(), oracle.to_int32(2 * vis)), (N, F)
+        assert np.array_equal(beam.cpu().numpy(), oracle.beam(volt, 4)), (N, F)
