@@ -13,11 +13,14 @@
 //
 // with natural input a = 2 * station + pol.  V_AB with pos(A) >= pos(B) is a
 // stored triangle element; otherwise it is the conjugate of the element
-// (pos(B), pos(A)).  One thread writes the four polarisation products of one
-// station pair (32 contiguous bytes); the inverse permutation lives in shared
-// memory.  The kernel is bound by HBM (reads of
-// the triangles, which the gather touches inside one channel's triangle at a
-// time, and the coalesced writes).
+// (pos(B), pos(A)).  One thread owns one station pair: it finds the pair's
+// four triangle elements once and then gathers them from every (dump,
+// channel) of each channel group its block visits, four (group, dump,
+// channel) triples at a time (16 loads in flight), writing the four
+// polarisation products of a group (32 contiguous bytes) after its last
+// triple; the inverse permutation lives in shared memory, built once per
+// block.  The kernel is bound by HBM (reads of the triangles, which the gather
+// touches inside one channel's triangle at a time, and the coalesced writes).
 #include "internal.cuh"
 
 namespace corr {
@@ -54,9 +57,7 @@ remap_kernel(RemapArgs args, int n, int n_chan, int f_avg, const int32_t *__rest
     const long long P = n_pairs(n);
     const int S = n / 2;
     const long long Q = n_pairs(S);
-    const int g = blockIdx.y;
-    // one thread per station pair: its four polarisation products are 32
-    // contiguous output bytes
+    const int n_groups = n_chan / f_avg, n_comb = args.n_dumps * f_avg;
     for (long long q = blockIdx.x * (long long)blockDim.x + threadIdx.x; q < Q;
          q += (long long)gridDim.x * blockDim.x) {
         int s1 = int((sqrtf(8.0f * float(q) + 1.0f) - 1.0f) * 0.5f);
@@ -71,21 +72,49 @@ remap_kernel(RemapArgs args, int n, int n_chan, int f_avg, const int32_t *__rest
             conj[pp] = i < j;
             k[pp] = conj[pp] ? n_pairs(j) + i : n_pairs(i) + j;
         }
+        // the (channel group, dump, channel) triples of this thread's station pair,
+        // groups blockIdx.y + j gridDim.y, taken four at a time (16 loads in flight)
+        const int n_j = (n_groups - int(blockIdx.y) + int(gridDim.y) - 1) / int(gridDim.y);
+        const int n_e = n_j * n_comb;
         int re[4] = {0, 0, 0, 0}, im[4] = {0, 0, 0, 0};
-        for (int d = 0; d < args.n_dumps; ++d) {
-            for (int f = g * f_avg; f < (g + 1) * f_avg; ++f) {
-                const int2 *tri = reinterpret_cast<const int2 *>(args.tri[d]) + (long long)f * P;
+        for (int e0 = 0; e0 < n_e; e0 += 4) {
+            int2 v[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u < n_e ? e0 + u : e0;   // past the end: repeat, not added
+                const int j = e / n_comb, c = e - j * n_comb;
+                const int g = int(blockIdx.y) + j * int(gridDim.y);
+                const int d = c / f_avg, f = g * f_avg + (c - d * f_avg);
+                // select the dump's pointer without indexing the parameter array
+                const int32_t *base = args.tri[0];
+#pragma unroll
+                for (int x = 1; x < kRemapMaxDumps; ++x)
+                    if (x == d) base = args.tri[x];
+                const int2 *tri = reinterpret_cast<const int2 *>(base) + (long long)f * P;
+#pragma unroll
+                for (int pp = 0; pp < 4; ++pp) v[u][pp] = __ldg(tri + k[pp]);
+            }
+#pragma unroll
+            for (int u = 0; u < 4; ++u) {
+                const int e = e0 + u;
+                if (e >= n_e) break;
 #pragma unroll
                 for (int pp = 0; pp < 4; ++pp) {
-                    const int2 v = __ldg(tri + k[pp]);
-                    re[pp] += v.x;
-                    im[pp] += v.y;
+                    re[pp] += v[u][pp].x;
+                    im[pp] += v[u][pp].y;
+                }
+                const int j = e / n_comb;
+                if (e - j * n_comb == n_comb - 1) {
+                    // the group's last triple: write its four products and start the next
+                    const int g = int(blockIdx.y) + j * int(gridDim.y);
+                    int4 *o = reinterpret_cast<int4 *>(out) + ((long long)g * Q + q) * 2;
+                    o[0] = make_int4(re[0], conj[0] ? -im[0] : im[0], re[1], conj[1] ? -im[1] : im[1]);
+                    o[1] = make_int4(re[2], conj[2] ? -im[2] : im[2], re[3], conj[3] ? -im[3] : im[3]);
+#pragma unroll
+                    for (int pp = 0; pp < 4; ++pp) re[pp] = im[pp] = 0;
                 }
             }
         }
-        int4 *o = reinterpret_cast<int4 *>(out) + ((long long)g * Q + q) * 2;
-        o[0] = make_int4(re[0], conj[0] ? -im[0] : im[0], re[1], conj[1] ? -im[1] : im[1]);
-        o[1] = make_int4(re[2], conj[2] ? -im[2] : im[2], re[3], conj[3] ? -im[3] : im[3]);
     }
 }
 
@@ -101,7 +130,11 @@ cudaError_t launch_remap(const int32_t *const *tri, int n_dumps, int n, int n_ch
     const long long Q = n_pairs(n / 2);
     const long long want = (Q + kRemapThreads - 1) / kRemapThreads;
     const int bx = int(want < 4096 ? want : 4096);
-    const dim3 grid(unsigned(bx), unsigned(n_chan / f_avg));
+    // a block builds the permutation table once and visits several channel
+    // groups: about 1600 blocks at 256 inputs
+    const int groups = n_chan / f_avg;
+    const int by = groups < 48 ? groups : 48;
+    const dim3 grid{unsigned(bx), unsigned(by)};
     remap_kernel<<<grid, kRemapThreads, size_t(n) * sizeof(int), s>>>(args, n, n_chan, f_avg, nat_of_pfb, out);
     return cudaGetLastError();
 }

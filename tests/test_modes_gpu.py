@@ -17,7 +17,12 @@ def _rand(shape, seed):
 
 
 @pytest.mark.parametrize("shape,n_avg", [((36, 5, 48), 1), ((36, 5, 48), 4), ((20, 3, 13), 5),
-                                         ((7, 300, 256), 7), ((1, 1, 1), 1)])
+                                         ((7, 300, 256), 7), ((1, 1, 1), 1),
+                                         # 1, 2, 4, 8 and 32 lanes per row (2 chunks a lane at 1024),
+                                         # 13 chunks a row, a block's 128 channels and a ragged rest
+                                         ((8, 300, 16), 2), ((6, 50, 96), 3), ((4, 33, 64), 1),
+                                         ((9, 130, 128), 3), ((5, 70, 512), 5), ((3, 40, 1024), 1),
+                                         ((5, 20, 208), 5)])
 @pytest.mark.parametrize("zero_invalid", [False, True])
 def test_beam_exact(shape, n_avg, zero_invalid):
     volt = _rand(shape, sum(shape) + n_avg)
@@ -55,7 +60,7 @@ def _tri_of(volt_np, path="auto"):
 
 
 @pytest.mark.parametrize("N,F,T", [(8, 4, 30), (128, 6, 200), (70, 2, 33)])
-@pytest.mark.parametrize("f_avg,n_dumps", [(1, 1), (2, 2), (1, 3)])
+@pytest.mark.parametrize("f_avg,n_dumps", [(1, 1), (2, 2), (1, 3), (3, 2), (1, 8)])
 def test_remap_exact_custom_order(N, F, T, f_avg, n_dumps):
     if F % f_avg:
         pytest.skip("channels not divisible")
