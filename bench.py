@@ -432,7 +432,7 @@ def measure_extras(arrays, volts, outs, stream_, dev, peaks, src, full=True):
         from synth import packets as pkts
         host = volts[0][:500].cpu().numpy()
         blk = torch.empty((500, f, n), dtype=torch.uint8, device=dev)
-        seen = torch.empty(corr.PKT_SLOTS, dtype=torch.int32, device=dev)
+        seen = torch.empty(corr.PKT_SLOTS, dtype=torch.uint8, device=dev)
         cnt = torch.empty(corr.PKT_COUNTERS, dtype=torch.int32, device=dev)
         for key, order in (("packet_ingest", pkts.arrival_order), ("packet_ingest_lane_order", pkts.packetise)):
             stream = torch.from_numpy(order(host, 0)).to(dev)

@@ -392,7 +392,7 @@ int corr_incoherent_beam(const uint8_t *d_volt, int n_time, int n_chan, int n_in
 #define CORR_PKT_CHANNELS 3072
 #define CORR_PKT_INPUTS 256
 #define CORR_PKT_SLOTS (CORR_PKT_FRAMES * (CORR_PKT_CHANNELS / 4) * 4)
-#define CORR_PKT_SEEN_BYTES (CORR_PKT_SLOTS * 4)
+#define CORR_PKT_SEEN_BYTES CORR_PKT_SLOTS   /* one mark byte per slot */
 #define CORR_PKT_GOOD 0
 #define CORR_PKT_BAD_HEADER 1
 #define CORR_PKT_BAD_CHECKSUM 2

@@ -582,14 +582,14 @@ def ingest_packets(packets: torch.Tensor, bank: int, out: torch.Tensor | None = 
     if out is None:
         out = torch.empty((PKT_FRAMES, PKT_CHANNELS, PKT_INPUTS), dtype=torch.uint8, device=dev)
     if seen is None:
-        seen = torch.empty(PKT_SLOTS, dtype=torch.int32, device=dev)
+        seen = torch.empty(PKT_SLOTS, dtype=torch.uint8, device=dev)
     if counters is None:
         counters = torch.empty(PKT_COUNTERS, dtype=torch.int32, device=dev)
     if tuple(out.shape) != (PKT_FRAMES, PKT_CHANNELS, PKT_INPUTS) or out.dtype != torch.uint8:
         raise ValueError("out must be uint8 [500][3072][256]")
-    if (seen.numel() * seen.element_size() < PKT_SLOTS * 4 or counters.numel() < PKT_COUNTERS
+    if (seen.numel() * seen.element_size() < PKT_SLOTS or counters.numel() < PKT_COUNTERS
             or counters.dtype != torch.int32):
-        raise ValueError(f"seen must hold 4 bytes per slot and counters {PKT_COUNTERS} int32")
+        raise ValueError(f"seen must hold one byte per slot and counters {PKT_COUNTERS} int32")
     _check(load().corr_ingest_packets(ctypes.c_void_p(packets.data_ptr()), packets.shape[0], bank,
                                       ctypes.c_void_p(out.data_ptr()), ctypes.c_void_p(seen.data_ptr()),
                                       ctypes.c_void_p(counters.data_ptr()), _stream_handle(stream)),

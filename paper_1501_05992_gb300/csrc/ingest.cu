@@ -16,12 +16,12 @@
 // decodes the header from the words its neighbours hold, and stores its bytes
 // with two 16-byte stores.  Sharing a warp among four packets divides the
 // header decode and the reduction, which bound the one-packet-per-warp form.
-// A slot is marked filled with a plain store (no value comes back, so no lane
-// waits on it).  A second pass, one thread per slot (frame, group of four
-// channels, PFB), writes the slots no good packet filled with 0x88, the
-// appendix's invalid code (CORR_ZERO_INVALID turns it into zeros), and counts
-// them; the repeats are the good packets minus the distinct filled slots,
-// added up in the same pass.
+// A slot is marked filled with a plain one-byte store (no value comes back, so
+// no lane waits on it).  A second pass, one thread per (frame, group of four
+// channels) reading the four PFBs' marks as one word, writes the slots no good
+// packet filled with 0x88, the appendix's invalid code (CORR_ZERO_INVALID
+// turns it into zeros), and counts them; the repeats are the good packets
+// minus the distinct filled slots, added up in the same pass.
 #include "internal.cuh"
 
 namespace corr {
@@ -64,7 +64,7 @@ struct PacketWords {
 template <int L, bool kAligned8>
 __global__ void __launch_bounds__(kIngestThreads)
 ingest_kernel(const uint32_t *__restrict__ pk, long long n_packets, int bank, uint8_t *__restrict__ volt,
-              uint32_t *__restrict__ seen, int *__restrict__ counters)
+              uint8_t *__restrict__ seen, int *__restrict__ counters)
 {
     constexpr int P = 32 / L, W = 64 / L;
     const int lane = threadIdx.x & 31, sub = lane / L, j = lane % L;
@@ -114,7 +114,7 @@ ingest_kernel(const uint32_t *__restrict__ pk, long long n_packets, int bank, ui
             if (code == CORR_PKT_GOOD) {
                 const int cgroup = 32 * chan + 4 * mgt + grp;
                 const long long slot = ((long long)frame * kGroups + cgroup) * 4 + pfb;
-                if (j == 0) seen[slot] = 1u;
+                if (j == 0) seen[slot] = 1;
                 // data word l holds channel f2 = l / 16, inputs 64 pfb + 4 (l % 16) .. + 3
                 const int l0 = W * j;
                 uint4 *o = reinterpret_cast<uint4 *>(volt +
@@ -133,28 +133,32 @@ ingest_kernel(const uint32_t *__restrict__ pk, long long n_packets, int bank, ui
     if (threadIdx.x < 5 && block_counts[threadIdx.x]) atomicAdd(counters + threadIdx.x, block_counts[threadIdx.x]);
 }
 
-// One thread per slot (frame, group of four channels, PFB): a slot nobody
-// filled gets its four 64-byte runs of 0x88.
+// One thread per (frame, group of four channels): its four slots (one per PFB)
+// are the four mark bytes of one word, and a slot nobody filled gets its four
+// 64-byte runs of 0x88.
 __global__ void __launch_bounds__(kIngestThreads)
-ingest_missing_kernel(uint8_t *__restrict__ volt, const uint32_t *__restrict__ seen, int *__restrict__ counters)
+ingest_missing_kernel(uint8_t *__restrict__ volt, const uint32_t *__restrict__ seen4, int *__restrict__ counters)
 {
     int missing = 0;
-    for (long long slot = blockIdx.x * (long long)kIngestThreads + threadIdx.x; slot < CORR_PKT_SLOTS;
-         slot += (long long)gridDim.x * kIngestThreads) {
-        if (seen[slot]) continue;
-        const int pfb = int(slot & 3);
-        const long long fg = slot >> 2;                 // frame * kGroups + cgroup
-        const long long frame = fg / kGroups, cgroup = fg % kGroups;
+    for (long long fg = blockIdx.x * (long long)kIngestThreads + threadIdx.x; fg < CORR_PKT_SLOTS / 4;
+         fg += (long long)gridDim.x * kIngestThreads) {
+        const uint32_t marks = seen4[fg];
+        if ((marks & 0x000000FFu) && (marks & 0x0000FF00u) && (marks & 0x00FF0000u) && (marks & 0xFF000000u))
+            continue;
+        const long long frame = fg / kGroups, cgroup = fg % kGroups;   // fg = frame * kGroups + cgroup
         const uint4 inv = make_uint4(0x88888888u, 0x88888888u, 0x88888888u, 0x88888888u);
+        for (int pfb = 0; pfb < 4; ++pfb) {
+            if ((marks >> (8 * pfb)) & 0xFFu) continue;
 #pragma unroll
-        for (int f2 = 0; f2 < 4; ++f2) {
-            uint4 *dst = reinterpret_cast<uint4 *>(volt + (frame * kChannels + 4 * cgroup + f2) * kInputs + 64 * pfb);
-            dst[0] = inv;
-            dst[1] = inv;
-            dst[2] = inv;
-            dst[3] = inv;
+            for (int f2 = 0; f2 < 4; ++f2) {
+                uint4 *dst = reinterpret_cast<uint4 *>(volt + (frame * kChannels + 4 * cgroup + f2) * kInputs + 64 * pfb);
+                dst[0] = inv;
+                dst[1] = inv;
+                dst[2] = inv;
+                dst[3] = inv;
+            }
+            ++missing;
         }
-        ++missing;
     }
     __shared__ int block_missing;
     if (threadIdx.x == 0) block_missing = 0;
@@ -172,12 +176,13 @@ ingest_missing_kernel(uint8_t *__restrict__ volt, const uint32_t *__restrict__ s
     }
 }
 
-// The slot marks (4-byte aligned) and the counters, zeroed in one launch.
+// The slot marks (one byte each, cleared four at a time) and the counters, in
+// one launch.
 __global__ void __launch_bounds__(kIngestThreads)
-ingest_clear_kernel(uint32_t *__restrict__ seen, int *__restrict__ counters)
+ingest_clear_kernel(uint32_t *__restrict__ seen4, int *__restrict__ counters)
 {
-    for (int e = blockIdx.x * kIngestThreads + threadIdx.x; e < CORR_PKT_SLOTS; e += gridDim.x * kIngestThreads)
-        seen[e] = 0u;
+    for (int e = blockIdx.x * kIngestThreads + threadIdx.x; e < CORR_PKT_SLOTS / 4; e += gridDim.x * kIngestThreads)
+        seen4[e] = 0u;
     if (blockIdx.x == 0 && threadIdx.x < CORR_PKT_COUNTERS) counters[threadIdx.x] = 0;
 }
 
@@ -186,7 +191,8 @@ ingest_clear_kernel(uint32_t *__restrict__ seen, int *__restrict__ counters)
 cudaError_t launch_ingest(const uint8_t *packets, long long n_packets, int bank, uint8_t *volt, void *seen,
                           int32_t *counters, cudaStream_t s)
 {
-    ingest_clear_kernel<<<(CORR_PKT_SLOTS + kIngestThreads - 1) / kIngestThreads, kIngestThreads, 0, s>>>(
+    static_assert(CORR_PKT_SLOTS % 4 == 0, "four slots per mark word");
+    ingest_clear_kernel<<<(CORR_PKT_SLOTS / 4 + kIngestThreads - 1) / kIngestThreads, kIngestThreads, 0, s>>>(
         static_cast<uint32_t *>(seen), counters);
     cudaError_t e = cudaGetLastError();
     if (e != cudaSuccess) return e;
@@ -200,14 +206,14 @@ cudaError_t launch_ingest(const uint8_t *packets, long long n_packets, int bank,
         const uint32_t *p32 = reinterpret_cast<const uint32_t *>(packets);
         if ((reinterpret_cast<uintptr_t>(packets) & 7) == 0)
             ingest_kernel<kL, true><<<grid, kIngestThreads, 0, s>>>(p32, n_packets, bank, volt,
-                                                                     static_cast<uint32_t *>(seen), counters);
+                                                                     static_cast<uint8_t *>(seen), counters);
         else
             ingest_kernel<kL, false><<<grid, kIngestThreads, 0, s>>>(p32, n_packets, bank, volt,
-                                                                      static_cast<uint32_t *>(seen), counters);
+                                                                      static_cast<uint8_t *>(seen), counters);
         e = cudaGetLastError();
         if (e != cudaSuccess) return e;
     }
-    ingest_missing_kernel<<<(CORR_PKT_SLOTS + kIngestThreads - 1) / kIngestThreads, kIngestThreads, 0, s>>>(
+    ingest_missing_kernel<<<(CORR_PKT_SLOTS / 4 + kIngestThreads - 1) / kIngestThreads, kIngestThreads, 0, s>>>(
         volt, static_cast<const uint32_t *>(seen), counters);
     e = cudaGetLastError();
     if (e != cudaSuccess) return e;
