@@ -106,7 +106,7 @@ struct TcArray {
 // Samples per padded copy for the tensor-core path when n % 16 != 0: the
 // whole integration if it fits kTcPadCap bytes, else chunks of a multiple
 // of 64 samples.
-constexpr size_t kTcPadCap = size_t(256) << 20;
+constexpr size_t kTcPadCap = size_t(4) << 30;
 // One persistent launch over every (channel, tile pair) of up to
 // kTcMaxArrays arrays (nt <= kTcMaxSamples each; arrays with nt == 0 skipped).
 cudaError_t launch_xeng_tc_batch(const TcArray *arrays, int count, DeviceStatus *status,
