@@ -102,8 +102,9 @@ int corr_destroy(corr_ctx *ctx);
  * this device (CORR_PATH_TC_FP8 needs an sm_103 device).  The tensor-core
  * path reads the voltage rows through TMA, which needs rows on 16-byte
  * boundaries: with n_inputs % 16 != 0 each call's samples are first copied
- * into rows of round_up(n_inputs, 16) bytes in the workspace (up to 256 MiB,
- * in chunks of a multiple of 64 samples), and in a batch such arrays are
+ * into rows of round_up(n_inputs, 16) bytes in the workspace (up to 4 GiB:
+ * a whole integration where it fits, else chunks of a multiple of 64
+ * samples), and in a batch such arrays are
  * correlated in launches of their own.  AUTO picks the tensor-core path from
  * 64 inputs on.  Valid only between integrations (corr_samples() == 0), else
  * CORR_E_STATE.  The default is CORR_PATH_AUTO. */
